@@ -1,0 +1,431 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: published
+generator outputs, closed forms, invariants of Eq. (1)-(2), brute force on
+tiny lattices, symmetries of the square lattice, and textbook hydrodynamic
+solutions.  Citations are to the paper (arXiv:0807.4471).
+"""
+import math
+import os
+from fractions import Fraction as Fr
+
+import numpy as np
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+W9 = {0: Fr(4, 9), 1: Fr(1, 9), 2: Fr(1, 36)}
+P25 = {1: Fr(4, 63), 2: Fr(4, 135), 4: Fr(1, 180), 5: Fr(2, 945), 8: Fr(1, 15120)}
+BELT1 = [(1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
+BELT2 = [(2, 0), (0, 2), (-2, 0), (0, -2), (2, 1), (1, 2), (-1, 2), (-2, 1),
+         (-2, -1), (-1, -2), (1, -2), (2, -1), (2, 2), (-2, 2), (-2, -2), (2, -2)]
+
+
+def params(O, caption, nx, ny, **kw):
+    c = dict(caption)
+    c.update(kw)
+    return O.make_params(nx, ny, **c)
+
+
+# ------------------------------------------------------------------ RNG
+def test_splitmix64_published_vectors(O):
+    golden = 0x9E3779B97F4A7C15
+    n = 0
+    with open(os.path.join(HERE, "golden", "splitmix64.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            seed, k, out = line.split()
+            z = (int(seed) + int(k) * golden) % 2**64
+            assert O.mix64(z) == int(out, 16)
+            n += 1
+    assert n == 7
+
+
+def test_uniform_statistics_and_init_range(O, caption):
+    u = np.array([O.uniform(7, i) for i in range(40000)])
+    assert u.min() >= 0.0 and u.max() < 1.0
+    assert abs(u.mean() - 0.5) < 5 * math.sqrt(1 / 12 / u.size)
+    assert abs(u.var() - 1 / 12) < 0.01 * 1 / 12
+    P = params(O, caption, 48, 40)
+    f = O.init_seeded(P, 3)
+    rho, jx, jy = O.moments(P, f)
+    r0, a = caption["rho0"], P.init_amp
+    assert rho.min() >= r0 * (1 - a) - 1e-15 and rho.max() < r0 * (1 + a) + 1e-15
+    assert np.abs(jx).max() < 1e-15 and np.abs(jy).max() < 1e-15
+    # counter index (s*ny + y)*nx + x: species B is not a copy of A, and
+    # site (x=5, y=9) of species B uses counter (1*40 + 9)*48 + 5
+    expect = r0 * (1 + a * (2 * O.uniform(3, (1 * 40 + 9) * 48 + 5) - 1))
+    assert abs(rho[1, 9, 5] - expect) < 1e-15
+    assert not np.allclose(rho[0], rho[1])
+
+
+# ----------------------------------------------------------- equilibrium
+@pytest.mark.parametrize("rho,ux,uy", [(1.0, 0.0, 0.0), (0.7, 0.05, -0.02),
+                                       (1.3, -0.1, 0.08), (0.02, 0.2, 0.1)])
+def test_equilibrium_closed_form_moments(O, rho, ux, uy):
+    """sum f = rho, sum f c = rho u, sum f c c = rho c_s^2 I + rho u u."""
+    cx, cy = O.velocities()
+    cx, cy = cx[:9], cy[:9]
+    f = O.feq(rho, ux, uy)
+    assert abs(f.sum() - rho) < 1e-15
+    assert abs((f * cx).sum() - rho * ux) < 1e-15
+    assert abs((f * cy).sum() - rho * uy) < 1e-15
+    assert abs((f * cx * cx).sum() - (rho / 3 + rho * ux * ux)) < 1e-15
+    assert abs((f * cy * cy).sum() - (rho / 3 + rho * uy * uy)) < 1e-15
+    assert abs((f * cx * cy).sum() - rho * ux * uy) < 1e-15
+    if ux == 0 and uy == 0:
+        w, _ = O.weights()
+        assert np.array_equal(f, w * rho)
+
+
+def test_psi_limits(O, caption):
+    """Psi(0) = 0, Psi'(0) = P/rho0, Psi -> P for rho >> rho0, P = sqrt(rho0)
+    (definition after Eq. (2)) or rho0 (psi_form = 1)."""
+    for form, pref in ((0, math.sqrt(0.7)), (1, 0.7)):
+        P = params(O, caption, 8, 8, psi_form=form)
+        assert O.psi(P, 0.0) == 0.0
+        h = 1e-7
+        assert abs(O.psi(P, h) / h - pref / 0.7) < 1e-6
+        assert abs(O.psi(P, 60 * 0.7) - pref) < 1e-15
+
+
+# ------------------------------------------------------------ force stencil
+def _kernel(Ga, Gr):
+    """Displacement -> coupling weight of the like-species force, as Fractions."""
+    K = {}
+    for c in BELT1:
+        K[c] = Fr(Ga) * W9[c[0] ** 2 + c[1] ** 2] + Fr(Gr) * P25[c[0] ** 2 + c[1] ** 2]
+    for c in BELT2:
+        K[c] = Fr(Gr) * P25[c[0] ** 2 + c[1] ** 2]
+    return {c: float(v) for c, v in K.items()}
+
+
+def _inv_psi(psi, rho0, pref):
+    return -rho0 * np.log(1.0 - psi / pref)
+
+
+@pytest.mark.parametrize("mode", [(1, 0), (0, 1), (2, 3), (5, 1)])
+def test_force_single_fourier_mode(O, caption, mode):
+    """Psi = a + b cos(k.r) gives sum_i K_i Psi(r+c_i) c_i
+    = -b sin(k.r) sum_i K_i sin(k.c_i) c_i (Eq. (2), like-species part), and
+    rho_s' = a' + b' cos(k.r) gives the cross part with the w weights."""
+    nx, ny = 24, 20
+    k = np.array([2 * np.pi * mode[0] / nx, 2 * np.pi * mode[1] / ny])
+    y, x = np.mgrid[0:ny, 0:nx]
+    phase = k[0] * x + k[1] * y
+    rho0 = caption["rho0"]
+    pref = math.sqrt(rho0)
+    # like-species part only
+    P = params(O, caption, nx, ny, GX=0.0)
+    a, b = 0.45, 0.12
+    psiA = a + b * np.cos(phase)
+    psiB = 0.5 - 0.07 * np.cos(phase)
+    rho = np.stack([_inv_psi(psiA, rho0, pref), _inv_psi(psiB, rho0, pref)])
+    Fx, Fy = O.forces(P, rho)
+    for s, (ps, bb) in enumerate(((psiA, b), (psiB, -0.07))):
+        K = _kernel(caption["Ga"][s], caption["Gr"][s])
+        Sx = sum(v * math.sin(k[0] * c[0] + k[1] * c[1]) * c[0] for c, v in K.items())
+        Sy = sum(v * math.sin(k[0] * c[0] + k[1] * c[1]) * c[1] for c, v in K.items())
+        ex = -ps * (-bb * np.sin(phase) * Sx)
+        ey = -ps * (-bb * np.sin(phase) * Sy)
+        assert np.abs(Fx[s] - ex).max() < 2e-14
+        assert np.abs(Fy[s] - ey).max() < 2e-14
+    # cross part only
+    P = params(O, caption, nx, ny, Ga=(0.0, 0.0), Gr=(0.0, 0.0))
+    rho = np.stack([0.7 + 0.05 * np.cos(phase), 0.6 - 0.03 * np.cos(phase)])
+    Fx, Fy = O.forces(P, rho)
+    Wk = {c: float(W9[c[0] ** 2 + c[1] ** 2]) for c in BELT1}
+    Sx = sum(v * math.sin(k[0] * c[0] + k[1] * c[1]) * c[0] for c, v in Wk.items())
+    Sy = sum(v * math.sin(k[0] * c[0] + k[1] * c[1]) * c[1] for c, v in Wk.items())
+    g = caption["GX"] / rho0
+    for s, bo in ((0, -0.03), (1, 0.05)):
+        ex = -g * rho[s] * (-bo * np.sin(phase) * Sx)
+        ey = -g * rho[s] * (-bo * np.sin(phase) * Sy)
+        assert np.abs(Fx[s] - ex).max() < 1e-14
+        assert np.abs(Fy[s] - ey).max() < 1e-14
+
+
+def _brute_force(rho, caption, psi_of, mirror_rows):
+    """O(N^2) pair sum over all sites r' (and their mirror images beyond the
+    Couette walls): F_s(r) = -Psi_s(r) sum_r' K_s(r'-r) Psi_s(r') (r'-r)
+    - (G_X/rho0) rho_s(r) sum_r' w(r'-r) rho_s'(r') (r'-r), with the
+    minimum-image displacement in the periodic directions."""
+    _, ny, nx = rho.shape
+    psi = psi_of(rho)
+    Fx = np.zeros_like(rho)
+    Fy = np.zeros_like(rho)
+    Ks = [_kernel(caption["Ga"][s], caption["Gr"][s]) for s in range(2)]
+    Wk = {c: float(W9[c[0] ** 2 + c[1] ** 2]) for c in BELT1}
+    g = caption["GX"] / caption["rho0"]
+    for s in range(2):
+        for y in range(ny):
+            for x in range(nx):
+                sx = sy = qx = qy = 0.0
+                for yp in range(ny):
+                    images = [yp]
+                    if mirror_rows:
+                        images += [-1 - yp, 2 * ny - 1 - yp]
+                    for yi in images:
+                        for xp in range(nx):
+                            dx = (xp - x + nx // 2) % nx - nx // 2
+                            dy = yi - y if mirror_rows else (yi - y + ny // 2) % ny - ny // 2
+                            if (dx, dy) in Ks[s]:
+                                sx += Ks[s][(dx, dy)] * psi[s, yp, xp] * dx
+                                sy += Ks[s][(dx, dy)] * psi[s, yp, xp] * dy
+                            if (dx, dy) in Wk:
+                                qx += Wk[(dx, dy)] * rho[1 - s, yp, xp] * dx
+                                qy += Wk[(dx, dy)] * rho[1 - s, yp, xp] * dy
+                Fx[s, y, x] = -psi[s, y, x] * sx - g * rho[s, y, x] * qx
+                Fy[s, y, x] = -psi[s, y, x] * sy - g * rho[s, y, x] * qy
+    return Fx, Fy
+
+
+@pytest.mark.parametrize("boundary", [0, 1])
+def test_force_brute_force_pairs(O, caption, boundary):
+    nx, ny = 8, 8
+    rng = np.random.default_rng(11)
+    rho = 0.7 * (1 + 0.3 * (2 * rng.random((2, ny, nx)) - 1))
+    P = params(O, caption, nx, ny, boundary=boundary)
+    rho0 = caption["rho0"]
+    Fx, Fy = O.forces(P, rho)
+    bx, by = _brute_force(rho, caption, lambda r: math.sqrt(rho0) * (1 - np.exp(-r / rho0)),
+                          mirror_rows=(boundary == 1))
+    assert np.abs(Fx - bx).max() < 1e-14
+    assert np.abs(Fy - by).max() < 1e-14
+
+
+def test_force_signs_two_blobs(O, caption):
+    """Positive G codes for repulsion, negative for attraction (text after
+    Eq. (2)): a blob of A pushes B away; a like-species bump with G^a < 0
+    attracts its neighbours."""
+    nx = ny = 16
+    y, x = np.mgrid[0:ny, 0:nx]
+    blob = 0.5 + 0.4 * np.exp(-((x - 8) ** 2 + (y - 8) ** 2) / 4.0)
+    rho = np.stack([blob, np.full((ny, nx), 0.5)])
+    P = params(O, caption, nx, ny, Ga=(0.0, 0.0), Gr=(0.0, 0.0))
+    Fx, Fy = O.forces(P, rho)
+    assert Fx[1, 8, 10] > 0 and Fx[1, 8, 6] < 0      # B pushed away from A
+    assert Fy[1, 10, 8] > 0 and Fy[1, 6, 8] < 0
+    P = params(O, caption, nx, ny, Ga=(-3.0, -3.0), Gr=(0.0, 0.0), GX=0.0)
+    Fx, Fy = O.forces(P, np.stack([blob, blob]))
+    assert Fx[0, 8, 10] < 0 and Fx[0, 8, 6] > 0      # pulled toward the bump
+    P = params(O, caption, nx, ny, Ga=(0.0, 0.0), Gr=(3.0, 3.0), GX=0.0)
+    Fx, Fy = O.forces(P, np.stack([blob, blob]))
+    assert Fx[0, 8, 10] > 0 and Fx[0, 8, 6] < 0      # repulsion pushes away
+
+
+def test_zero_net_interaction_force(O, caption):
+    """Pair sums are antisymmetric: on a periodic lattice the like-species
+    force sums to zero per species and the cross force over both species."""
+    rng = np.random.default_rng(2)
+    rho = 0.7 * (1 + 0.5 * (2 * rng.random((2, 32, 40)) - 1))
+    P = params(O, caption, 40, 32, GX=0.0)
+    Fx, Fy = O.forces(P, rho)
+    assert abs(Fx[0].sum()) < 1e-13 and abs(Fy[1].sum()) < 1e-13
+    P = params(O, caption, 40, 32)
+    Fx, Fy = O.forces(P, rho)
+    assert abs(Fx.sum()) < 1e-13 and abs(Fy.sum()) < 1e-13
+    assert abs(Fx[0].sum()) > 1e-3   # the cross part alone is not zero per species
+
+
+# -------------------------------------------------------------- streaming
+def test_streaming_moves_along_c(O, caption):
+    """Left-hand side of Eq. (1): f_i(r + c_i, t+1) receives f_i(r, t)."""
+    P = params(O, caption, 6, 5)
+    cx, cy = O.velocities()
+    for i in range(9):
+        f = O.empty_f(P)
+        f[2, 3, 1, i] = 1.0
+        O.stream_only(P, f, 1)
+        assert f[(2 + cy[i]) % 5, (3 + cx[i]) % 6, 1, i] == 1.0
+        assert f.sum() == 1.0
+
+
+@pytest.mark.parametrize("boundary,period", [(0, 8), (1, 16)])
+def test_streaming_is_a_permutation(O, caption, boundary, period):
+    P = params(O, caption, 8, 8, boundary=boundary)
+    f0 = np.random.default_rng(1).random((8, 8, 2, 9))
+    f = f0.copy()
+    O.stream_only(P, f, 1)
+    assert np.array_equal(np.sort(f.ravel()), np.sort(f0.ravel()))
+    if boundary == 0:   # mass per direction is conserved by periodic streaming
+        assert np.allclose(f.sum(axis=(0, 1)), f0.sum(axis=(0, 1)), rtol=0, atol=1e-13)
+    O.stream_only(P, f, period - 1)
+    assert np.array_equal(f, f0)
+
+
+# ----------------------------------------------------------- conservation
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_mass_and_momentum_conservation(O, caption, scheme):
+    nx, ny = 40, 32
+    # conservation does not depend on the coupling values; the literal source
+    # term is not stable at the full caption couplings, so it runs at half
+    half = {k: (tuple(0.5 * v for v in caption[k]) if k in ("Ga", "Gr") else caption[k])
+            for k in caption}
+    P = O.make_params(nx, ny, **(half if scheme == 1 else caption), force_scheme=scheme,
+                      tau=(1.0, 0.8))
+    rng = np.random.default_rng(4)
+    rhoA = 0.7 * (1 + 0.03 * (2 * rng.random((ny, nx)) - 1))
+    rhoB = 0.7 * (1 + 0.03 * (2 * rng.random((ny, nx)) - 1))
+    ux = 0.02 + 0.01 * rng.standard_normal((ny, nx))
+    uy = -0.01 + 0.01 * rng.standard_normal((ny, nx))
+    f = O.init_fields(P, rhoA, rhoB, ux, uy)
+    t0 = O.totals(P, f)
+    assert abs(t0[2]) > 1.0
+    assert O.run(P, f, 200) == 0
+    t1 = O.totals(P, f)
+    assert abs(t1[0] - t0[0]) / t0[0] < 1e-13
+    assert abs(t1[1] - t0[1]) / t0[1] < 1e-13
+    assert abs(t1[2] - t0[2]) < 1e-10 and abs(t1[3] - t0[3]) < 1e-10
+
+
+def test_couette_mass_conservation(O, caption):
+    P = params(O, caption, 24, 16, boundary=1, u_wall=0.05)
+    f = O.init_seeded(P, 9)
+    m0 = O.totals(P, f)
+    O.run(P, f, 150)
+    m1 = O.totals(P, f)
+    assert abs(m1[0] - m0[0]) / m0[0] < 1e-13 and abs(m1[1] - m0[1]) / m0[1] < 1e-13
+
+
+def test_uniform_state_is_a_fixed_point(O, caption):
+    P = params(O, caption, 16, 16)
+    f = O.init_fields(P, np.full((16, 16), 0.7), np.full((16, 16), 0.5))
+    f0 = f.copy()
+    O.run(P, f, 1000)
+    assert np.abs(f - f0).max() <= 1e-15
+
+
+# --------------------------------------------------------------- symmetry
+@pytest.mark.parametrize("op", ["rot90", "transpose", "flipx", "flipy"])
+def test_square_lattice_symmetry(O, caption, op):
+    n = 24
+    P = params(O, caption, n, n)
+    rng = np.random.default_rng(8)
+    rhoA = 0.7 * (1 + 0.03 * (2 * rng.random((n, n)) - 1))
+    rhoB = 0.7 * (1 + 0.03 * (2 * rng.random((n, n)) - 1))
+    T = {"rot90": np.rot90, "transpose": np.transpose,
+         "flipx": lambda a: a[:, ::-1], "flipy": lambda a: a[::-1, :]}[op]
+    f = O.init_fields(P, rhoA, rhoB)
+    g = O.init_fields(P, np.ascontiguousarray(T(rhoA)), np.ascontiguousarray(T(rhoB)))
+    O.run(P, f, 30)
+    O.run(P, g, 30)
+    ra, rb, _, _ = O.fields(P, f)
+    sa, sb, _, _ = O.fields(P, g)
+    assert np.abs(T(ra) - sa).max() < 1e-12 and np.abs(T(rb) - sb).max() < 1e-12
+
+
+def test_species_swap_symmetry(O, caption):
+    """Swapping A and B together with their couplings swaps the result."""
+    n = 20
+    P = params(O, caption, n, n, tau=(1.0, 0.9))
+    Q = params(O, caption, n, n, tau=(0.9, 1.0), Ga=caption["Ga"][::-1], Gr=caption["Gr"][::-1])
+    rng = np.random.default_rng(3)
+    rhoA = 0.7 * (1 + 0.03 * (2 * rng.random((n, n)) - 1))
+    rhoB = 0.7 * (1 + 0.03 * (2 * rng.random((n, n)) - 1))
+    f = O.init_fields(P, rhoA, rhoB)
+    g = O.init_fields(Q, rhoB, rhoA)
+    O.run(P, f, 40)
+    O.run(Q, g, 40)
+    ra, rb, ux, uy = O.fields(P, f)
+    sa, sb, vx, vy = O.fields(Q, g)
+    assert np.array_equal(ra, sb) and np.array_equal(rb, sa)
+    assert np.array_equal(ux, vx) and np.array_equal(uy, vy)
+
+
+# ----------------------------------------------------------- hydrodynamics
+@pytest.mark.parametrize("tau", [1.0, 0.8])
+def test_couette_profile_and_wall_stress(O, tau):
+    """Passive fluid (all G = 0) between halfway walls moving -U and +U:
+    u_x = U (2y + 1 - H)/H and wall stress rho nu0 gamma with
+    nu0 = c_s^2 (tau - 1/2), gamma = 2U/H."""
+    nx, H, U = 4, 16, 0.01
+    P = O.make_params(nx, H, Ga=(0.0, 0.0), Gr=(0.0, 0.0), GX=0.0, rho0=0.5,
+                      tau=(tau, tau), boundary=1, u_wall=U, init_amp=0.0,
+                      stress_t0=9000)
+    f = O.init_seeded(P, 0)
+    acc = O.Accum()
+    O.run(P, f, 10000, acc=acc)
+    _, _, ux, uy = O.fields(P, f)
+    y = np.arange(H)
+    expect = U * (2 * y + 1 - H) / H
+    assert np.abs(ux - expect[:, None]).max() < 1e-12
+    assert np.abs(uy).max() < 1e-14
+    nu0 = (tau - 0.5) / 3
+    sbot = acc.sum_bot / acc.samples
+    stop = acc.sum_top / acc.samples
+    assert acc.samples == 1000
+    want = 1.0 * nu0 * 2 * U / H     # total density 1.0
+    assert abs(sbot - want) < 1e-12 * 1e3 * want and abs(stop + want) < 1e-9 * want
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_poiseuille_second_order(O, scheme):
+    """Body-force driven channel flow between resting halfway walls converges
+    to u = g (y + 1/2)(H - 1/2 - y) / (2 nu0) at second order in 1/H."""
+    errs = []
+    for H in (8, 16, 32):
+        nu0 = 1.0 / 6.0
+        g = 1e-6
+        P = O.make_params(2, H, Ga=(0.0, 0.0), Gr=(0.0, 0.0), GX=0.0, rho0=0.5,
+                          boundary=1, u_wall=0.0, init_amp=0.0, g_x=g,
+                          force_scheme=scheme)
+        f = O.init_seeded(P, 0)
+        O.run(P, f, int(40 * H * H))
+        _, _, ux, _ = O.fields(P, f)
+        y = np.arange(H)
+        ex = g * (y + 0.5) * (H - 0.5 - y) / (2 * nu0)
+        errs.append(np.abs(ux[:, 0] - ex).max() / ex.max())
+    assert errs[-1] < 1e-2
+    assert errs[0] / errs[1] > 3.0 or errs[0] < 1e-10
+    assert errs[1] / errs[2] > 3.0 or errs[1] < 1e-10
+
+
+@np.errstate(invalid="ignore")
+def _mode_growth(O, P, rho_a, rho_b, steps):
+    f = O.init_fields(P, rho_a, rho_b)
+    ra0, rb0, _, _ = O.fields(P, f)
+    O.run(P, f, steps)
+    ra, rb, _, _ = O.fields(P, f)
+    return (np.abs(ra - ra.mean()).max() / np.abs(ra0 - ra0.mean()).max(),
+            np.abs((ra - rb) - (ra - rb).mean()).max() /
+            np.abs((ra0 - rb0) - (ra0 - rb0).mean()).max())
+
+
+def test_bulk_eos_single_species_threshold(O):
+    """The bulk pressure of Eq. (3), p = c_s^2 rho + (c_s^2/2) G Psi^2, turns
+    unstable where dp/drho < 0, i.e. G < -1/(Psi Psi') = -4.30 at rho = rho0
+    for Psi = sqrt(rho0)(1 - e^{-rho/rho0})."""
+    nx, ny = 64, 4
+    x = np.arange(nx)
+    pert = 1.0 * (1 + 1e-4 * np.cos(2 * np.pi * x / nx))[None, :].repeat(ny, 0)
+    grow = {}
+    for G in (-4.0, -4.6):
+        P = O.make_params(nx, ny, Ga=(G, G), Gr=(0.0, 0.0), GX=0.0, rho0=1.0)
+        grow[G] = _mode_growth(O, P, pert, pert, 1500)[0]
+    assert grow[-4.0] < 1.5
+    assert grow[-4.6] > 20.0
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+@pytest.mark.parametrize("tau", [1.0, 0.8])
+def test_cross_repulsion_demixing_threshold(O, tau, scheme):
+    """Symmetric mixture rho_A = rho_B = rho with only the cross force of
+    Eq. (2).  Expanding the streaming to second order and using the
+    post-collision momentum j* = (1 - 1/tau) j + rho u' + F gives, for the
+    composition mode, d_t rho_A = c_s^2 (tau - 1/2) lap rho_A - tau div F_A
+    with F_A = -(G_X/rho0) rho c_s^2 grad rho_B at long wavelength, i.e. a
+    mutual diffusivity c_s^2 [(tau - 1/2) - tau G_X rho / rho0].  The mode
+    decays below G_X rho/rho0 = (tau - 1/2)/tau and grows above it."""
+    nx, ny = 32, 4
+    x = np.arange(nx)
+    d = 1e-6 * np.cos(2 * np.pi * x / nx)[None, :].repeat(ny, 0)
+    thr = (tau - 0.5) / tau     # rho = rho0
+    out = {}
+    for m in (0.85, 1.25):
+        P = O.make_params(nx, ny, Ga=(0.0, 0.0), Gr=(0.0, 0.0), GX=m * thr, rho0=0.7,
+                          tau=(tau, tau), force_scheme=scheme)
+        out[m] = _mode_growth(O, P, 0.7 + d, 0.7 - d, 3000)[1]
+    assert out[0.85] < 0.5
+    assert out[1.25] > 5.0
