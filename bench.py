@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the two-species multi-range LB step on GB300.
+
+Workload (default): the rho0 sweep at the paper's resolution -- five periodic
+512 x 512 lattices, FP32, rho0 in {0.55, 0.65, 0.70, 0.75, 0.83}, the Fig. 2
+caption couplings, Psi = rho0 (1 - exp(-rho/rho0)), seeded init (seed 1).
+One bench step = one LB time step of all five lattices (5 x 512^2 two-species
+site updates).  Metric: MLUPS (million two-species site updates per second).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import lbinputs  # noqa: E402
+
+BYTES_PER_SITE = {"fp64": 288, "fp32": 144, "fp16": 72, "bf16": 72}
+KERNEL_SRC = os.path.join(ROOT, "paper_0807_4471_gb300", "csrc", "lb_kernels.cu")
+
+
+def kernel_hash() -> str:
+    with open(KERNEL_SRC, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel: str, precision: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; None otherwise."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    e = d.get(f"{kernel}:{precision}:{workload}")
+    if not e or e.get("kernel_sha") != kernel_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.th.join(timeout=2)
+
+    def summary(self):
+        mhz, maxmhz, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                maxmhz.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not mhz:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": max(maxmhz),
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def sweep_lattices(lb, precision: str, nx: int, ny: int, count: int):
+    cfg = lbinputs.CFG_SWEEP
+    lats = []
+    for rho0 in cfg["rho0s"][:count]:
+        p = lb.make_params(nx, ny, precision, rho0=rho0, psi_form=lb.LB_PSI_RHO0)
+        lats.append(lb.Lattice(p))
+    return lats
+
+
+def time_steps(torch, lats, steps: int):
+    """CUDA-event time of `steps` bench steps on the lattices' stream."""
+    stream = lats[0].stream
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        for g in lats:
+            g.step(1)
+    ev1.record(stream)
+    ev1.synchronize()
+    return ev0.elapsed_time(ev1) / 1e3
+
+
+def cpu_oracle_sample(nx: int, ny: int, rho0: float, steps: int, seed: int):
+    import oracle as O
+    c = lbinputs.CAPTION
+    P = O.make_params(nx, ny, Ga=c["Ga"], Gr=c["Gr"], GX=c["GX"], rho0=rho0, psi_form=1)
+    f = O.init_seeded(P, seed)
+    t0 = time.perf_counter()
+    O.run(P, f, steps)
+    dt = time.perf_counter() - t0
+    return nx * ny * steps / dt / 1e6, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    cfg = lbinputs.CFG_SWEEP
+    nx, ny = args.nx, args.ny
+    rho0s = cfg["rho0s"]
+    import oracle as O
+    O.build()
+    for k in range(args.warmup):
+        cpu_oracle_sample(nx, ny, rho0s[k % len(rho0s)], 1, cfg["seed"])
+    tot = 0.0
+    for k in range(args.steps):
+        _, dt = cpu_oracle_sample(nx, ny, rho0s[k % len(rho0s)], 1, cfg["seed"])
+        tot += dt
+    value = nx * ny * args.steps / tot / 1e6
+    sample = (f"one {nx}x{ny} lattice of the five-lattice rho0 sweep per step "
+              f"(rho0 cycling over {list(rho0s)}), one LB step each, FP64 oracle, 1 thread")
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": value, "unit": "MLUPS",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"rho0 sweep, 5 x {nx}x{ny} periodic", "nx": nx, "ny": ny},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def peak_lattice(torch, lb, precision: str, n: int, steps: int):
+    """MLUPS and HBM fraction of one large periodic lattice (inputs >> L2)."""
+    p = lb.make_params(n, n, precision, psi_form=lb.LB_PSI_RHO0)
+    g = lb.Lattice(p).init_seeded(lbinputs.CFG_PEAK["seed"])
+    g.step(3)
+    torch.cuda.synchronize()
+    dt = time_steps(torch, [g], steps)
+    g.sync()
+    g.close()
+    mlups = n * n * steps / dt / 1e6
+    return mlups, mlups * 1e6 * BYTES_PER_SITE[precision] / 1e9
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=list(BYTES_PER_SITE))
+    ap.add_argument("--nx", type=int, default=lbinputs.CFG_SWEEP["nx"])
+    ap.add_argument("--ny", type=int, default=lbinputs.CFG_SWEEP["ny"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-peak", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--lattices", type=int, default=len(lbinputs.CFG_SWEEP["rho0s"]),
+                    help="number of sweep lattices stepped per bench step (profiling runs)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_0807_4471_gb300 as lb
+    from paper_0807_4471_gb300 import build as _b
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    _b.build()
+    lb.load()
+
+    cfg = lbinputs.CFG_SWEEP
+    nx, ny, prec = args.nx, args.ny, args.precision
+    lats = sweep_lattices(lb, prec, nx, ny, args.lattices)
+    for g in lats:
+        g.init_seeded(cfg["seed"])
+    for _ in range(args.warmup):
+        for g in lats:
+            g.step(1)
+    for g in lats:
+        g.sync()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    with ClockSampler(local) as clk:
+        dt = time_steps(torch, lats, args.steps)
+    barrier()
+    for g in lats:
+        g.sync()   # raises on a latched device error
+    if ws > 1:
+        t = torch.tensor([dt], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    sites = nx * ny * len(lats)
+    value = sites * args.steps * ws / dt / 1e6
+    launches = args.steps * len(lats)
+    avg_launch = dt / launches
+    hbm_peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_SITE[prec] * nx * ny / avg_launch / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                "traffic": ncu_traffic("k_step", prec, f"{nx}x{ny}"),
+                "bytes_per_launch_alg": BYTES_PER_SITE[prec] * nx * ny,
+                "kernel": f"k_step<{prec}>", "avg_launch_us": avg_launch * 1e6}
+
+    # end to end through the C ABI with host buffers: upload the initial
+    # fields, run the steps, read the densities back.
+    e2e = None
+    if not args.no_e2e:
+        host = []
+        for k, g in enumerate(lats):
+            u = lbinputs.uniforms(100 + k, (2, ny, nx))
+            r0 = cfg["rho0s"][k]
+            host.append((np.ascontiguousarray(r0 * (1 + 0.03 * (2 * u[0] - 1))),
+                         np.ascontiguousarray(r0 * (1 + 0.03 * (2 * u[1] - 1)))))
+        outA = [np.empty((ny, nx)) for _ in lats]
+        outB = [np.empty((ny, nx)) for _ in lats]
+        e_steps = args.steps
+        barrier()
+        t0 = time.perf_counter()
+        for (ra, rb), g in zip(host, lats):
+            g.init_fields(ra, rb)
+        for _ in range(e_steps):
+            for g in lats:
+                g.step(1)
+        for g, a, b in zip(lats, outA, outB):
+            lb.lb_fields(g.h, a, b, None, None)
+        e_dt = time.perf_counter() - t0
+        h2d = sum(a.nbytes + b.nbytes for a, b in host)
+        d2h = sum(a.nbytes + b.nbytes for a, b in zip(outA, outB))
+        e2e = {"value": sites * e_steps / e_dt / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": h2d / e_steps, "d2h_bytes_per_step": d2h / e_steps,
+               "note": "per lattice: lb_init_fields from host FP64 fields, the steps, "
+                       "lb_fields of rho_A and rho_B to host; bytes amortised per step"}
+    for g in lats:
+        g.close()
+
+    extra = {}
+    if rank == 0 and not args.no_peak:
+        for p in ("fp32", "fp16"):
+            mlups, gbs = peak_lattice(torch, lb, p, lbinputs.CFG_PEAK["nx"], 50)
+            extra[f"peak_{p}_4096"] = {"MLUPS": mlups, "GB_per_s_alg": gbs,
+                                       "frac_hbm": gbs / hbm_peak}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        steps_cpu = 60
+        mlups, cdt = cpu_oracle_sample(nx, ny, 0.70, steps_cpu, cfg["seed"])
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"one {nx}x{ny} lattice (rho0 0.70) of the sweep, {steps_cpu} steps, "
+                         f"{cdt:.1f} s, FP64 oracle single thread"}
+
+    if rank == 0:
+        line = {
+            "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f16-offset storage, f32 math",
+                      "bf16": "bf16-offset storage, f32 math"}[prec],
+            "data": "synthetic",
+            "config": {"workload": f"rho0 sweep, 5 x {nx}x{ny} periodic lattices, "
+                                   f"{prec} storage, one LB step of all five per bench step",
+                       "nx": nx, "ny": ny, "lattices": len(lats),
+                       "rho0": list(cfg["rho0s"]), "couplings": "Fig. 2 caption",
+                       "l2": "inputs larger than L2: 5 lattices x 2 population buffers "
+                             "(189 MB at FP32) cycled every step",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk.summary(), "extra": extra,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,179 @@
+/*
+ * lb.h -- C ABI of the GB300 two-species multi-range pseudo-potential
+ * lattice Boltzmann library (liblbgb.so).
+ *
+ * The model is the one of Benzi, Chibbaro & Succi, "Mesoscopic lattice
+ * Boltzmann modeling of flowing soft systems" (arXiv:0807.4471):
+ *  - Eq. (1): per species s in {A, B}, D2Q9 BGK relaxation with time tau_s
+ *    toward the local equilibrium, a body force F_s, and free streaming;
+ *  - Eq. (2): F_s = F^a_s + F^r_s + F^X_s, a like-species attraction G^a_s on
+ *    the first belt (D2Q9 weights w), a like-species repulsion G^r_s on both
+ *    belts (24 neighbours, 8th-order isotropic weights p) acting on the
+ *    pseudo-potential Psi_s(rho) = P (1 - exp(-rho/rho0)), and a cross-species
+ *    repulsion (G_AB/rho0) rho_s sum w_i rho_s'(r + c_i) c_i on the first belt;
+ *  - the Fig. 2 caption gives the couplings G_A1, G_A2, G_B1, G_B2, G^X.
+ * Every force term carries an overall minus sign, so that positive G is
+ * repulsive as the text after Eq. (2) states.  The paper has no walls;
+ * plane-Couette moving-wall bounce-back is an addition of this library.
+ *
+ * Conventions for every entry point:
+ *  - The status is returned; nothing crosses the ABI as an exception.
+ *  - A handle owns its device memory (unless created with lb_create_in, in
+ *    which case the caller owns the workspace and must keep it alive until
+ *    lb_destroy).  The caller owns every host buffer.
+ *  - Work is enqueued on the CUDA stream given at creation (NULL = legacy
+ *    default stream).  lb_step returns once its kernels are enqueued; device
+ *    errors (non-finite density, a TMA wait that timed out) are latched on the
+ *    device and returned by the next synchronising call (lb_fields,
+ *    lb_populations, lb_stress, lb_sync).
+ *  - Calls on one handle are not thread-safe; different handles are
+ *    independent.
+ *  - Host field arrays are FP64, row-major [ny][nx] (x fastest), whatever the
+ *    storage precision.
+ */
+#ifndef LB_H
+#define LB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_handle lb_handle;
+
+typedef enum {
+    LB_OK = 0,
+    LB_ERR_INVALID = -1,     /* bad argument or parameter                      */
+    LB_ERR_NOMEM = -2,       /* device allocation failed / workspace too small */
+    LB_ERR_CUDA = -3,        /* a CUDA runtime call failed                      */
+    LB_ERR_NONFINITE = -4,   /* a density became NaN or Inf                     */
+    LB_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up             */
+    LB_ERR_STATE = -6,       /* call out of order (e.g. step before init)      */
+    LB_ERR_UNSUPPORTED = -7  /* no kernel for this configuration               */
+} lb_status;
+
+/* Storage precision of the populations.  Arithmetic is FP64 for LB_FP64 and
+ * FP32 otherwise; the half formats store f_i - w_i rho_ref rounded to
+ * nearest-even and decode to FP32. */
+typedef enum { LB_FP64 = 0, LB_FP32 = 1, LB_FP16_OFFSET = 2, LB_BF16_OFFSET = 3 } lb_precision;
+
+/* LB_COUETTE: x periodic, halfway bounce-back walls at y = -1/2 (velocity
+ * -u_wall) and y = ny - 1/2 (velocity +u_wall). */
+typedef enum { LB_PERIODIC = 0, LB_COUETTE = 1 } lb_boundary;
+
+/* Prefactor P of Psi = P (1 - exp(-rho/rho0)): sqrt(rho0) as printed after
+ * Eq. (2), or rho0. */
+typedef enum { LB_PSI_SQRT_RHO0 = 0, LB_PSI_RHO0 = 1 } lb_psi_form;
+
+/* How F_s enters Eq. (1): Shan-Chen equilibrium-velocity shift
+ * u_s^eq = u' + tau_s F_s / rho_s with the common velocity
+ * u' = sum_s (j_s/tau_s) / sum_s (rho_s/tau_s), or the additive term
+ * F_is = w_i (c_i . F_s) / c_s^2 with f^eq at u'. */
+typedef enum { LB_FORCE_SHIFT = 0, LB_FORCE_SOURCE = 1 } lb_force_scheme;
+
+typedef struct {
+    int32_t nx, ny;            /* lattice size, each >= 8; x is fastest        */
+    int32_t boundary;          /* lb_boundary                                  */
+    int32_t precision;         /* lb_precision                                 */
+    int32_t psi_form;          /* lb_psi_form                                  */
+    int32_t force_scheme;      /* lb_force_scheme                              */
+    int32_t init_shear;        /* lb_init_seeded velocity: 0 rest, 1 the linear
+                                  Couette profile u_x = u_wall (2y+1-ny)/ny     */
+    int32_t stress_every;      /* wall-stress sample period in steps (>= 1)    */
+    int64_t stress_t0;         /* first step index that is sampled            */
+    double tau_A, tau_B;       /* relaxation times, > 1/2                      */
+    double G_A1, G_A2;         /* species A: attraction (belt 1), repulsion (belts 1+2) */
+    double G_B1, G_B2;         /* species B: attraction, repulsion             */
+    double G_X;                /* cross-species coupling G_AB                  */
+    double rho0;               /* reference density (> 0)                      */
+    double u_wall;             /* Couette wall speed                           */
+    double init_amp;           /* lb_init_seeded: rho = rho0 (1 + amp (2u-1))  */
+    double rho_ref;            /* offset base of the half formats (0 => rho0)  */
+    double g_x;                /* uniform body acceleration along x            */
+    double kolmo_amp;          /* Kolmogorov acceleration amplitude            */
+    double kolmo_k;            /* a_x += kolmo_amp sin(2 pi kolmo_k y / ny)    */
+} lb_params;
+
+typedef struct {
+    double mass_A, mass_B;     /* sum of rho_A, rho_B at the current time      */
+    double mom_x, mom_y;       /* sum_r sum_s (j_s + F_s/2)                    */
+    double sigma_bot, sigma_top; /* time-averaged x-momentum given to the bottom
+                                  / top wall per unit length and step          */
+    double sigma_mean;         /* (sigma_bot - sigma_top)/2                    */
+    double nu_eff;             /* sigma_mean / (shear rate * mean density)     */
+    double response_R;         /* nu0 / nu_eff, nu0 = c_s^2 (tau - 1/2)        */
+    int64_t samples;           /* number of wall-stress samples averaged       */
+    int64_t step;              /* current time step                            */
+} lb_stress_out;
+
+/* Fill *p with the Fig. 2 caption couplings, tau = 1, rho0 = 0.70, a periodic
+ * 128 x 128 FP32 lattice, init_amp = 0.03, stress_every = 1. */
+void lb_params_default(lb_params* p);
+
+/* Device bytes a handle needs for *p (both population buffers and the
+ * reduction area).  LB_ERR_INVALID if *p is not valid. */
+lb_status lb_workspace_size(const lb_params* p, size_t* bytes);
+
+/* Validate *p, allocate device memory with cudaMalloc, build the TMA
+ * descriptors.  stream is a cudaStream_t (NULL = default stream).  On error
+ * *out is NULL and nothing is leaked. */
+lb_status lb_create(const lb_params* p, void* stream, lb_handle** out);
+
+/* As lb_create, but the device memory is the caller's: `workspace` must be a
+ * device pointer aligned to 256 bytes holding at least lb_workspace_size
+ * bytes.  LB_ERR_NOMEM if `bytes` is too small. */
+lb_status lb_create_in(const lb_params* p, void* stream, void* workspace, size_t bytes,
+                       lb_handle** out);
+
+/* Random initial densities ("random initial conditions for the two
+ * densities", text after Eq. (5)): rho_s(x,y) = rho0 (1 + init_amp (2u - 1))
+ * with u = (z >> 11) 2^-53, z = mix64(seed ^ mix64(idx + 0x9E3779B97F4A7C15)),
+ * idx = (s ny + y) nx + x, mix64 the SplitMix64 finaliser; velocity zero (or
+ * the Couette profile if init_shear); populations at equilibrium.  Resets the
+ * step counter and the stress averages. */
+lb_status lb_init_seeded(lb_handle* h, uint64_t seed);
+
+/* Initial state from host FP64 fields [ny][nx]: f = f^eq(rho_s, u).  ux and
+ * uy may be NULL (zero).  Resets the step counter and the stress averages.
+ * Synchronises the stream. */
+lb_status lb_init_fields(lb_handle* h, const double* rho_A, const double* rho_B,
+                         const double* ux, const double* uy);
+
+/* Advance n >= 0 time steps of Eq. (1) (asynchronous on the stream). */
+lb_status lb_step(lb_handle* h, int64_t n);
+
+/* Copy the fields at the current time to host FP64 arrays [ny][nx]: the
+ * densities and the barycentric velocity u = sum_s (j_s + F_s/2) / sum_s rho_s.
+ * Any pointer may be NULL.  Synchronises. */
+lb_status lb_fields(lb_handle* h, double* rho_A, double* rho_B, double* ux, double* uy);
+
+/* Copy the populations f_is(r, t) at the current time (after streaming,
+ * before collision), decoded to FP64, to a host array [2][9][ny][nx]
+ * (species, D2Q9 direction in the order rest, +x, +y, -x, -y, (+1,+1),
+ * (-1,+1), (-1,-1), (+1,-1)).  Synchronises. */
+lb_status lb_populations(lb_handle* h, double* f);
+
+/* Totals at the current time and the time-averaged wall stress of the
+ * Couette walls (response R = nu0/nu_eff as defined after Fig. 3).
+ * Synchronises. */
+lb_status lb_stress(lb_handle* h, lb_stress_out* out);
+
+/* Wait for the handle's stream and return any latched device error. */
+lb_status lb_sync(lb_handle* h);
+
+/* Number of completed time steps. */
+int64_t lb_time(const lb_handle* h);
+
+/* Release the handle (NULL is accepted).  Synchronises. */
+lb_status lb_destroy(lb_handle* h);
+
+/* Static description of a status code. */
+const char* lb_status_string(lb_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LB_H */

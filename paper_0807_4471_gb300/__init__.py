@@ -1,0 +1,270 @@
+"""GB300-native two-species multi-range pseudo-potential lattice Boltzmann.
+
+Thin ctypes binding of the C ABI in ``include/lb.h`` (liblbgb.so).  Every
+step of the model runs in the library's CUDA kernels; this module only
+marshals arguments.  PyTorch supplies device memory (the workspace handed to
+``lb_create_in``) and the CUDA stream.  There is no CPU fallback: if the
+library is missing the import of a function raises ``RuntimeError``.
+
+Model: Benzi, Chibbaro & Succi, "Mesoscopic lattice Boltzmann modeling of
+flowing soft systems" (arXiv:0807.4471), Eqs. (1)-(2).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_LIB_PATH = _build.LIB
+_lock = threading.Lock()
+_lib = None
+
+LB_OK, LB_ERR_INVALID, LB_ERR_NOMEM, LB_ERR_CUDA = 0, -1, -2, -3
+LB_ERR_NONFINITE, LB_ERR_TIMEOUT, LB_ERR_STATE, LB_ERR_UNSUPPORTED = -4, -5, -6, -7
+LB_FP64, LB_FP32, LB_FP16_OFFSET, LB_BF16_OFFSET = 0, 1, 2, 3
+LB_PERIODIC, LB_COUETTE = 0, 1
+LB_PSI_SQRT_RHO0, LB_PSI_RHO0 = 0, 1
+LB_FORCE_SHIFT, LB_FORCE_SOURCE = 0, 1
+PRECISIONS = {"fp64": LB_FP64, "fp32": LB_FP32, "fp16": LB_FP16_OFFSET, "bf16": LB_BF16_OFFSET}
+
+
+class lb_params(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("boundary", C.c_int32),
+        ("precision", C.c_int32), ("psi_form", C.c_int32), ("force_scheme", C.c_int32),
+        ("init_shear", C.c_int32), ("stress_every", C.c_int32), ("stress_t0", C.c_int64),
+        ("tau_A", C.c_double), ("tau_B", C.c_double), ("G_A1", C.c_double),
+        ("G_A2", C.c_double), ("G_B1", C.c_double), ("G_B2", C.c_double),
+        ("G_X", C.c_double), ("rho0", C.c_double), ("u_wall", C.c_double),
+        ("init_amp", C.c_double), ("rho_ref", C.c_double), ("g_x", C.c_double),
+        ("kolmo_amp", C.c_double), ("kolmo_k", C.c_double),
+    ]
+
+
+class lb_stress_out(C.Structure):
+    _fields_ = [
+        ("mass_A", C.c_double), ("mass_B", C.c_double), ("mom_x", C.c_double),
+        ("mom_y", C.c_double), ("sigma_bot", C.c_double), ("sigma_top", C.c_double),
+        ("sigma_mean", C.c_double), ("nu_eff", C.c_double), ("response_R", C.c_double),
+        ("samples", C.c_int64), ("step", C.c_int64),
+    ]
+
+
+class LbError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {lb_status_string(status)} (status {status})")
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load liblbgb.so (build it first with ``build()``); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"CUDA extension {_LIB_PATH} is missing: run "
+                               "paper_0807_4471_gb300.build.build() (there is no CPU fallback)")
+        L = C.CDLL(_LIB_PATH)
+        P = C.POINTER(lb_params)
+        H = C.c_void_p
+        dp = C.POINTER(C.c_double)
+        sig = {
+            "lb_params_default": (None, [P]),
+            "lb_workspace_size": (C.c_int, [P, C.POINTER(C.c_size_t)]),
+            "lb_create": (C.c_int, [P, C.c_void_p, C.POINTER(H)]),
+            "lb_create_in": (C.c_int, [P, C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(H)]),
+            "lb_init_seeded": (C.c_int, [H, C.c_uint64]),
+            "lb_init_fields": (C.c_int, [H, dp, dp, dp, dp]),
+            "lb_step": (C.c_int, [H, C.c_int64]),
+            "lb_fields": (C.c_int, [H, dp, dp, dp, dp]),
+            "lb_populations": (C.c_int, [H, dp]),
+            "lb_stress": (C.c_int, [H, C.POINTER(lb_stress_out)]),
+            "lb_sync": (C.c_int, [H]),
+            "lb_time": (C.c_int64, [H]),
+            "lb_destroy": (C.c_int, [H]),
+            "lb_status_string": (C.c_char_p, [C.c_int]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+        return L
+
+
+def _check(status: int, where: str):
+    if status != LB_OK:
+        raise LbError(status, where)
+
+
+def _dp(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+# --------------------------------------------------------------- C ABI names
+def lb_status_string(status: int) -> str:
+    return load().lb_status_string(status).decode()
+
+
+def lb_params_default() -> lb_params:
+    p = lb_params()
+    load().lb_params_default(C.byref(p))
+    return p
+
+
+def lb_workspace_size(p: lb_params) -> int:
+    n = C.c_size_t()
+    _check(load().lb_workspace_size(C.byref(p), C.byref(n)), "lb_workspace_size")
+    return n.value
+
+
+def lb_create(p: lb_params, stream: int = 0) -> int:
+    h = C.c_void_p()
+    _check(load().lb_create(C.byref(p), C.c_void_p(stream), C.byref(h)), "lb_create")
+    return h.value
+
+
+def lb_create_in(p: lb_params, stream: int, workspace_ptr: int, nbytes: int) -> int:
+    h = C.c_void_p()
+    _check(load().lb_create_in(C.byref(p), C.c_void_p(stream), C.c_void_p(workspace_ptr),
+                               nbytes, C.byref(h)), "lb_create_in")
+    return h.value
+
+
+def lb_init_seeded(h: int, seed: int):
+    _check(load().lb_init_seeded(C.c_void_p(h), seed), "lb_init_seeded")
+
+
+def lb_init_fields(h: int, rho_A, rho_B, ux=None, uy=None):
+    _check(load().lb_init_fields(C.c_void_p(h), _dp(rho_A), _dp(rho_B), _dp(ux), _dp(uy)),
+           "lb_init_fields")
+
+
+def lb_step(h: int, n: int):
+    _check(load().lb_step(C.c_void_p(h), n), "lb_step")
+
+
+def lb_fields(h: int, rho_A=None, rho_B=None, ux=None, uy=None):
+    _check(load().lb_fields(C.c_void_p(h), _dp(rho_A), _dp(rho_B), _dp(ux), _dp(uy)), "lb_fields")
+
+
+def lb_populations(h: int, f):
+    _check(load().lb_populations(C.c_void_p(h), _dp(f)), "lb_populations")
+
+
+def lb_stress(h: int) -> dict:
+    out = lb_stress_out()
+    _check(load().lb_stress(C.c_void_p(h), C.byref(out)), "lb_stress")
+    return {k: getattr(out, k) for k, _ in lb_stress_out._fields_}
+
+
+def lb_sync(h: int):
+    _check(load().lb_sync(C.c_void_p(h)), "lb_sync")
+
+
+def lb_time(h: int) -> int:
+    return load().lb_time(C.c_void_p(h))
+
+
+def lb_destroy(h: int):
+    _check(load().lb_destroy(C.c_void_p(h)), "lb_destroy")
+
+
+# ------------------------------------------------------------ convenience
+def make_params(nx: int, ny: int, precision="fp32", **kw) -> lb_params:
+    """lb_params from keyword arguments (the names of the struct fields);
+    unspecified fields keep lb_params_default's values."""
+    p = lb_params_default()
+    p.nx, p.ny = nx, ny
+    p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Lattice:
+    """One resident lattice.  Device memory is a torch uint8 tensor on the
+    current CUDA device; work runs on torch's current stream (or `stream`)."""
+
+    def __init__(self, params: lb_params, stream=None, device=None):
+        import torch
+        self.params = params
+        self.nx, self.ny = params.nx, params.ny
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self._stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        nbytes = lb_workspace_size(params)
+        with torch.cuda.device(dev):
+            self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        ptr = (self._ws.data_ptr() + 255) // 256 * 256
+        self.workspace_bytes = nbytes
+        self.h = lb_create_in(params, self._stream.cuda_stream, ptr, nbytes)
+
+    @property
+    def stream(self):
+        return self._stream
+
+    def init_seeded(self, seed: int):
+        lb_init_seeded(self.h, seed)
+        return self
+
+    def init_fields(self, rho_A, rho_B, ux=None, uy=None):
+        f = [None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+             for a in (rho_A, rho_B, ux, uy)]
+        lb_init_fields(self.h, *f)
+        return self
+
+    def step(self, n: int = 1):
+        lb_step(self.h, n)
+        return self
+
+    def fields(self):
+        out = [np.empty((self.ny, self.nx)) for _ in range(4)]
+        lb_fields(self.h, *out)
+        return out
+
+    def populations(self):
+        f = np.empty((2, 9, self.ny, self.nx))
+        lb_populations(self.h, f)
+        return f
+
+    def stress(self) -> dict:
+        return lb_stress(self.h)
+
+    def sync(self):
+        lb_sync(self.h)
+
+    @property
+    def t(self) -> int:
+        return lb_time(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lb_destroy(self.h)
+            self.h = None
+            self._ws = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,98 @@
+// lb_internal.h -- structures shared by the host side of the C ABI
+// (lb_api.cu) and the kernels (lb_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda.h>           // CUtensorMap (type only; the driver is reached via
+#include <cuda_runtime.h>   // cudaGetDriverEntryPointByVersion)
+
+#include "../../include/lb.h"
+
+namespace lbgb {
+
+// Device-resident counters and accumulators of one lattice.
+struct DevStats {
+    unsigned int err;       // bit 0: non-finite density, bit 1: TMA wait timeout
+    unsigned int ticket;    // CTA arrival counter of the last-block reductions
+    long long t;            // completed time steps
+    double sum_bot;         // sum of per-step bottom-wall samples
+    double sum_top;         // sum of per-step top-wall samples
+    long long samples;      // number of samples in the sums
+    double totals[4];       // last observe pass: mass_A, mass_B, mom_x, mom_y
+    double pad_[7];
+};
+static_assert(sizeof(DevStats) == 128, "DevStats is one 128-byte line");
+
+enum : unsigned int { ERR_NONFINITE = 1u, ERR_TIMEOUT = 2u };
+
+// Geometry of the ghost-padded population planes.  Plane q = s*9 + i holds
+// (ny + 2*kGY) rows of `pitch` elements; lattice site (x, y) sits at row
+// y + kGY, column x + gx.  The kGY = 3 rows and gx >= 3 columns on each side
+// hold periodic copies so that the tile loads never wrap.
+constexpr int kGY = 3;
+
+struct Geom {
+    int nx, ny;
+    int pitch;          // elements per padded row (row bytes a multiple of 16)
+    int rows;           // ny + 2*kGY
+    long long plane;    // elements per plane = rows * pitch
+    int gx;             // ghost columns on each side
+    int periodic;       // 1: periodic in y; 0: Couette walls in y
+};
+
+// Per-launch model coefficients, in the compute precision C.
+template <typename C>
+struct Coef {
+    C K[2][12];        // like-species pair weights G^a w(d) + G^r p(d), 12 reps d
+    C W[4];            // cross-species pair weights w(d), 4 reps d
+    C gx_rho0;         // G_X / rho0
+    C psi_ref;         // Psi(rho_ref)
+    C psi_scale;       // P exp(-rho_ref / rho0)
+    C inv_rho0;        // 1 / rho0
+    C rho_ref;         // reference density of the stored offsets
+    C tau[2];          // relaxation times
+    C omega[2];        // 1 / tau
+    C u_wall;          // Couette wall speed (top +, bottom -)
+    C g_x;             // uniform body acceleration
+    C kolmo_amp;       // Kolmogorov acceleration amplitude
+    C kolmo_w;         // 2 pi kolmo_k / ny
+    int source;        // 1: additive source term; 0: velocity shift
+    int has_accel;     // 1 if g_x or kolmo_amp is nonzero
+};
+
+// Observe-mode outputs (the kernel writes FP64 planes of nx*ny values).
+enum ObsKind : int { OBS_NONE = 0, OBS_FIELDS = 1, OBS_POPS = 2, OBS_TOTALS = 3 };
+
+template <typename C>
+struct StepArgs {
+    Geom g;
+    Coef<C> k;
+    void* fout;            // output population buffer (padded planes)
+    DevStats* st;
+    double* slots;         // per-CTA partial sums
+    int pull;              // 1: input holds post-collision f*(t-1); 0: f(t) in place
+    int obs;               // ObsKind; OBS_NONE = a time step
+    double* obs_out;       // observe output base
+    int q0, q1;            // OBS_POPS: planes [q0, q1) written
+    long long stress_t0;
+    int stress_every;
+};
+
+// Host launchers (lb_kernels.cu).
+int kernel_smem_bytes(int precision);
+int kernel_tile_x(int precision);
+int kernel_tile_y(int precision);
+int kernel_ghost_x(int precision);
+int kernel_elem_bytes(int precision);
+
+cudaError_t launch_step(int precision, const CUtensorMap* tin, const void* args,
+                        dim3 grid, cudaStream_t s);
+cudaError_t launch_init_seeded(int precision, const Geom& g, const void* coef,
+                               void* fout, double rho0, double amp, double u_wall,
+                               int init_shear, unsigned long long seed, cudaStream_t s);
+cudaError_t launch_init_fields(int precision, const Geom& g, const void* coef,
+                               void* fout, const double* fields, cudaStream_t s);
+
+}  // namespace lbgb
