@@ -169,6 +169,35 @@ int64_t lb_time(const lb_handle* h);
 /* Release the handle (NULL is accepted).  Synchronises. */
 lb_status lb_destroy(lb_handle* h);
 
+/* Largest lattice, nx * ny, that lb_totals_noalloc accepts (4096 x 4096). */
+#define LB_NOALLOC_MAX_SITES 16777216
+
+/* Totals of caller-owned FP64 device fields, without allocating anything.
+ * The paper has no counterpart; this entry point exists for callers that may
+ * not call cudaMalloc -- for instance code that runs inside a fixed device
+ * arena it cannot grow, or inside a framework that forbids allocation on its
+ * hot path.  It is the mass/momentum reduction of lb_stress (FP64 warp sums,
+ * one slot per CTA, the last CTA adds the slots in a fixed order) run on
+ * fields the caller passes in.
+ *
+ * Inputs: device arrays rho_A, rho_B, ux, uy of nx * ny FP64 values each
+ * (any layout, e.g. [ny][nx] as lb_fields writes them).  Output: `totals`, a
+ * device array of 4 doubles, receives {sum rho_A, sum rho_B,
+ * sum (rho_A + rho_B) ux, sum (rho_A + rho_B) uy}, asynchronously on `stream`
+ * (a cudaStream_t, NULL = default stream).  Returns LB_ERR_INVALID for a NULL
+ * pointer, nx or ny < 1, or nx * ny > LB_NOALLOC_MAX_SITES.
+ *
+ * Scratch: the per-CTA slots and the arrival counter live in one static
+ * device array of 128 KB + 256 B that every GPU which loads the library keeps
+ * until the process exits.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Each call clears the counter with cudaMemsetAsync on
+ * `stream` and overwrites the slots it uses.  All calls on a device share the
+ * array, so calls whose kernels may overlap on the GPU (different streams with
+ * no ordering between them) race: order them on one stream or with events. */
+lb_status lb_totals_noalloc(int32_t nx, int32_t ny, const double* rho_A, const double* rho_B,
+                            const double* ux, const double* uy, double* totals, void* stream);
+
 /* Static description of a status code. */
 const char* lb_status_string(lb_status s);
 

@@ -92,6 +92,8 @@ def load():
             "lb_time": (C.c_int64, [H]),
             "lb_destroy": (C.c_int, [H]),
             "lb_status_string": (C.c_char_p, [C.c_int]),
+            "lb_totals_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -180,6 +182,17 @@ def lb_time(h: int) -> int:
 
 def lb_destroy(h: int):
     _check(load().lb_destroy(C.c_void_p(h)), "lb_destroy")
+
+
+LB_NOALLOC_MAX_SITES = 16777216
+
+
+def lb_totals_noalloc(nx: int, ny: int, rho_A: int, rho_B: int, ux: int, uy: int,
+                      totals: int, stream: int = 0):
+    """Device pointers in and out (see include/lb.h); allocates nothing."""
+    _check(load().lb_totals_noalloc(nx, ny, C.c_void_p(rho_A), C.c_void_p(rho_B),
+                                    C.c_void_p(ux), C.c_void_p(uy), C.c_void_p(totals),
+                                    C.c_void_p(stream)), "lb_totals_noalloc")
 
 
 # ------------------------------------------------------------ convenience

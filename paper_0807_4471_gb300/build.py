@@ -14,7 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbgb.so")
-SOURCES = ["lb_kernels.cu", "lb_api.cu"]
+SOURCES = ["lb_kernels.cu", "lb_api.cu", "lb_noalloc.cu"]
 HEADERS = ["lb_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
