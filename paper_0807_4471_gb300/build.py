@@ -14,8 +14,15 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbgb.so")
-SOURCES = ["lb_kernels.cu", "lb_api.cu", "lb_noalloc.cu"]
-HEADERS = ["lb_internal.h"]
+# (source, extra defines, object name); the step kernels are compiled once
+# per storage precision so that the four compilations run in parallel.
+UNITS = [("lb_kernels.cu", [f"-DLB_PREC={p}"], f"lb_kernels_p{p}.o") for p in range(4)] + [
+    ("lb_dispatch.cu", [], "lb_dispatch.o"),
+    ("lb_api.cu", [], "lb_api.o"),
+    ("lb_noalloc.cu", [], "lb_noalloc.o"),
+]
+SOURCES = sorted({u[0] for u in UNITS})
+HEADERS = ["lb_internal.h", "lb_layout.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]
@@ -45,10 +52,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     cc = nvcc()
     procs = []
     objs = []
-    for src in SOURCES:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+    for src, defs, oname in UNITS:
+        obj = os.path.join(BUILD, oname)
         objs.append(obj)
-        cmd = [cc, *ARCH, *FLAGS, "-I", INCLUDE, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *defs, "-I", INCLUDE, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

@@ -26,12 +26,14 @@ struct lb_handle {
     double* slots;
     char* fbuf[2];
     size_t fbuf_bytes;
-    CUtensorMap tmap[2];
+    CUtensorMap tmap[2];   // load descriptors (tile + halo boxes) of buffers 0, 1
+    CUtensorMap smap[2];   // store descriptors (tile boxes) of buffers 0, 1
     int cur;               // index of the buffer holding the current state
     int pull;              // 1: cur holds post-collision f*(t-1); 0: f(t) in place
     bool inited;
     long long t;
-    dim3 grid;
+    dim3 grid;             // observe kernel: one CTA per tile
+    dim3 grid_step;        // persistent step kernel: one CTA per SM (at most one per tile)
     Coef<double> kd;
     Coef<float> kf;
     unsigned int err_latched;
@@ -173,7 +175,7 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-lb_status make_tmap(CUtensorMap* m, const lb_params* p, const Geom& g, void* base) {
+lb_status make_tmap(CUtensorMap* m, const lb_params* p, const Geom& g, void* base, bool store) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return LB_ERR_CUDA;
     const int es = kernel_elem_bytes(p->precision);
@@ -182,8 +184,8 @@ lb_status make_tmap(CUtensorMap* m, const lb_params* p, const Geom& g, void* bas
                                                        : CU_TENSOR_MAP_DATA_TYPE_UINT16;
     cuuint64_t dims[3] = {(cuuint64_t)g.pitch, (cuuint64_t)g.rows, 18};
     cuuint64_t strides[2] = {(cuuint64_t)g.pitch * es, (cuuint64_t)g.plane * es};
-    cuuint32_t box[3] = {(cuuint32_t)(kernel_tile_x(p->precision) + 2 * g.gx),
-                         (cuuint32_t)(kernel_tile_y(p->precision) + 2 * kGY), 9};
+    cuuint32_t box[3] = {(cuuint32_t)(kernel_tile_x(p->precision) + (store ? 0 : 2 * g.gx)),
+                         (cuuint32_t)(kernel_tile_y(p->precision) + (store ? 0 : 2 * kGY)), 9};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(m, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -224,7 +226,8 @@ lb_status launch(lb_handle* h, int obs, double* obs_out, int q0, int q1) {
         a.q0 = q0;
         a.q1 = q1;
         a.fout = obs == OBS_NONE ? h->fbuf[1 - h->cur] : nullptr;
-        e = launch_step(h->p.precision, &h->tmap[h->cur], &a, h->grid, h->stream);
+        e = launch_step(h->p.precision, &h->tmap[h->cur], &h->smap[1 - h->cur], &a, obs,
+                        obs == OBS_NONE ? h->grid_step : h->grid, h->stream);
     } else {
         StepArgs<float> a;
         fill_args(a, h, h->kf);
@@ -233,7 +236,8 @@ lb_status launch(lb_handle* h, int obs, double* obs_out, int q0, int q1) {
         a.q0 = q0;
         a.q1 = q1;
         a.fout = obs == OBS_NONE ? h->fbuf[1 - h->cur] : nullptr;
-        e = launch_step(h->p.precision, &h->tmap[h->cur], &a, h->grid, h->stream);
+        e = launch_step(h->p.precision, &h->tmap[h->cur], &h->smap[1 - h->cur], &a, obs,
+                        obs == OBS_NONE ? h->grid_step : h->grid, h->stream);
     }
     return cuda_status(e);
 }
@@ -300,6 +304,11 @@ static lb_status create_common(const lb_params* p, void* stream, void* ws, size_
     h->grid = make_grid(p);
     h->stream = reinterpret_cast<cudaStream_t>(stream);
     cudaGetDevice(&h->device);
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || sms < 1)
+        sms = 1;
+    const unsigned ntiles = h->grid.x * h->grid.y;
+    h->grid_step = dim3(ntiles < (unsigned)sms ? ntiles : (unsigned)sms, 1, 1);
     h->owns = owns;
     h->ws = reinterpret_cast<char*>(ws);
     h->ws_bytes = bytes;
@@ -316,8 +325,10 @@ static lb_status create_common(const lb_params* p, void* stream, void* ws, size_
     h->err_latched = 0;
     fill_coef(h->kd, p);
     fill_coef(h->kf, p);
-    lb_status s = make_tmap(&h->tmap[0], p, h->g, h->fbuf[0]);
-    if (s == LB_OK) s = make_tmap(&h->tmap[1], p, h->g, h->fbuf[1]);
+    lb_status s = make_tmap(&h->tmap[0], p, h->g, h->fbuf[0], false);
+    if (s == LB_OK) s = make_tmap(&h->tmap[1], p, h->g, h->fbuf[1], false);
+    if (s == LB_OK) s = make_tmap(&h->smap[0], p, h->g, h->fbuf[0], true);
+    if (s == LB_OK) s = make_tmap(&h->smap[1], p, h->g, h->fbuf[1], true);
     if (s == LB_OK) s = cuda_status(cudaMemsetAsync(h->ws, 0, L.total, h->stream));
     if (s != LB_OK) {
         if (owns) cudaFree(ws);
@@ -452,7 +463,7 @@ lb_status lb_stress(lb_handle* h, lb_stress_out* out) {
     out->mom_x = st.totals[2];
     out->mom_y = st.totals[3];
     out->samples = st.samples;
-    out->step = st.t;
+    out->step = h->t;
     if (st.samples > 0) {
         out->sigma_bot = st.sum_bot / (double)st.samples;
         out->sigma_top = st.sum_top / (double)st.samples;

@@ -80,19 +80,33 @@ struct StepArgs {
     int stress_every;
 };
 
-// Host launchers (lb_kernels.cu).
+// Host-side launch helpers (lb_dispatch.cu).
 int kernel_smem_bytes(int precision);
 int kernel_tile_x(int precision);
 int kernel_tile_y(int precision);
 int kernel_ghost_x(int precision);
 int kernel_elem_bytes(int precision);
 
-cudaError_t launch_step(int precision, const CUtensorMap* tin, const void* args,
-                        dim3 grid, cudaStream_t s);
-cudaError_t launch_init_seeded(int precision, const Geom& g, const void* coef,
-                               void* fout, double rho0, double amp, double u_wall,
-                               int init_shear, unsigned long long seed, cudaStream_t s);
-cudaError_t launch_init_fields(int precision, const Geom& g, const void* coef,
-                               void* fout, const double* fields, cudaStream_t s);
+// obs = OBS_NONE: the persistent step kernel over `grid` CTAs; otherwise the
+// observe kernel with one CTA per tile.
+// tin: load descriptor of the input buffer; tout: store descriptor of the
+// output buffer (unused by the observe kernel).
+cudaError_t launch_step(int precision, const CUtensorMap* tin, const CUtensorMap* tout,
+                        const void* args, int obs, dim3 grid, cudaStream_t s);
+cudaError_t launch_init_seeded(int precision, const Geom& g, const void* coef, void* fout,
+                               double rho0, double amp, double u_wall, int init_shear,
+                               unsigned long long seed, cudaStream_t s);
+cudaError_t launch_init_fields(int precision, const Geom& g, const void* coef, void* fout,
+                               const double* fields, cudaStream_t s);
+
+// Per-precision launchers, one explicit instantiation per compilation of
+// lb_kernels.cu (-DLB_PREC=P).
+template <int P>
+cudaError_t launch_step_prec(const CUtensorMap* tin, const CUtensorMap* tout, const void* args,
+                             int obs, dim3 grid, cudaStream_t s);
+template <int P>
+cudaError_t launch_init_prec(const Geom& g, const void* coef, void* fout, int mode,
+                             const double* fields, double rho0, double amp, double u_wall,
+                             int init_shear, unsigned long long seed, cudaStream_t s);
 
 }  // namespace lbgb
