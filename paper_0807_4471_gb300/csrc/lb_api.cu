@@ -182,9 +182,12 @@ lb_status make_tmap(CUtensorMap* m, const lb_params* p, const Geom& g, void* bas
     CUtensorMapDataType dt = p->precision == LB_FP64   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                              : p->precision == LB_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                                        : CU_TENSOR_MAP_DATA_TYPE_UINT16;
-    cuuint64_t dims[3] = {(cuuint64_t)g.pitch, (cuuint64_t)g.rows, 18};
-    cuuint64_t strides[2] = {(cuuint64_t)g.pitch * es, (cuuint64_t)g.plane * es};
-    cuuint32_t box[3] = {(cuuint32_t)(kernel_tile_x(p->precision) + (store ? 0 : 2 * g.gx)),
+    // 9 direction planes of interleaved (A, B) pairs: a row holds 2 * pitch
+    // elements.
+    cuuint64_t dims[3] = {(cuuint64_t)(2 * g.pitch), (cuuint64_t)g.rows, 9};
+    cuuint64_t strides[2] = {(cuuint64_t)(2 * g.pitch) * es,
+                             (cuuint64_t)g.rows * (cuuint64_t)(2 * g.pitch) * es};
+    cuuint32_t box[3] = {(cuuint32_t)(2 * (kernel_tile_x(p->precision) + (store ? 0 : 2 * g.gx))),
                          (cuuint32_t)(kernel_tile_y(p->precision) + (store ? 0 : 2 * kGY)), 9};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(m, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,

@@ -27,17 +27,18 @@ static_assert(sizeof(DevStats) == 128, "DevStats is one 128-byte line");
 
 enum : unsigned int { ERR_NONFINITE = 1u, ERR_TIMEOUT = 2u };
 
-// Geometry of the ghost-padded population planes.  Plane q = s*9 + i holds
-// (ny + 2*kGY) rows of `pitch` elements; lattice site (x, y) sits at row
-// y + kGY, column x + gx.  The kGY = 3 rows and gx >= 3 columns on each side
-// hold periodic copies so that the tile loads never wrap.
+// Geometry of the ghost-padded population planes.  Plane i (i = 0..8, the
+// D2Q9 direction) holds (ny + 2*kGY) rows of `pitch` interleaved (A, B)
+// pairs; lattice site (x, y) sits at row y + kGY, pair column x + gx.  The
+// kGY = 3 rows and gx >= 3 columns on each side hold periodic copies so that
+// the tile loads never wrap.
 constexpr int kGY = 3;
 
 struct Geom {
     int nx, ny;
-    int pitch;          // elements per padded row (row bytes a multiple of 16)
+    int pitch;          // (A, B) pairs per padded row (row bytes a multiple of 16)
     int rows;           // ny + 2*kGY
-    long long plane;    // elements per plane = rows * pitch
+    long long plane;    // pairs per direction plane = rows * pitch
     int gx;             // ghost columns on each side
     int periodic;       // 1: periodic in y; 0: Couette walls in y
 };

@@ -3,25 +3,24 @@
 // arXiv:0807.4471, Eqs. (1)-(2)).
 //
 // One launch of k_step advances every site of the lattice by one time step.
-// Layout in HBM: structure of arrays, 18 planes (species s, direction i), each
-// a ghost-padded [ny + 6][pitch] array of the storage type T.  The buffer read
-// by a step holds the post-collision populations f*(t-1) of the previous
-// step; streaming is done by pulling, f_i(r, t) = f*_i(r - c_i, t - 1).
+// Layout in HBM: 9 direction planes, each a ghost-padded [ny + 6][pitch]
+// array of interleaved (A, B) pairs of the storage type, holding offsets
+// h_i = f_i - w_i rho_ref.  The buffer read by a step holds the
+// post-collision populations f*(t-1) of the previous step; streaming is a
+// pull, f_i(r, t) = f*_i(r - c_i, t - 1).
 //
-// Per CTA (a TX x TY tile of sites):
-//  1. TMA: two 3-D box loads (one per species, 9 planes each) bring f* on the
-//     tile plus a 3-cell halo into shared memory.  The ghost columns/rows of
-//     the padded planes hold periodic copies, so a box never wraps.
-//  2. rho_s and Psi_s(rho_s) on the tile plus a 2-cell halo, from the pulled
-//     populations (halfway bounce-back rows at Couette walls; rho mirrored
-//     about a wall beyond it).
-//  3. per site: moments, the force of Eq. (2) from the shared rho/Psi tile
-//     (12 antisymmetric pairs of the 24-neighbour stencil, 4 pairs of the
-//     cross term), the forced BGK relaxation of Eq. (1), and the write of
-//     f*(t) into the other buffer together with its periodic ghost copies.
-//  4. FP64 block reductions (wall momentum exchange, or mass/momentum in the
-//     observe pass) into per-CTA slots; the last CTA to finish sums the slots
-//     in a fixed order and advances the device step counter.
+// k_step is persistent: one CTA per SM walks the TX x TY tiles.  Per tile:
+//  1. TMA: one 3-D box load brings f* on the tile plus a 3-cell halo (both
+//     species, 9 planes) into shared memory; the next tile's box loads into
+//     the second buffer meanwhile.  The ghost columns/rows of the padded
+//     planes hold periodic copies, so a box never wraps.
+//  2. density and pseudo-potential deviations on the tile plus a 2-cell halo
+//     (halfway bounce-back at Couette walls; mirrored beyond a wall).
+//  3. one site per thread: moments, the force of Eq. (2) from the shared
+//     tiles (12 antisymmetric pairs of the 24-neighbour stencil, 4 pairs of
+//     the cross term), the forced BGK relaxation of Eq. (1) into a staging
+//     tile, written back by a TMA bulk tensor store (plus ghost copies).
+//  4. Couette: FP64 wall-momentum sums, per-CTA slots, last CTA samples.
 // There is no dense contraction anywhere, so no tensor cores are used.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -109,57 +108,74 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 }
 
 // ---------------------------------------------------------- site helpers
-// Write one value of plane q at site (x, y) and its periodic ghost copies.
-template <typename T>
-__device__ __forceinline__ void put(T* base, const Geom& g, int q, int x, int y, T v) {
-    T* pl = base + (long long)q * g.plane;
-    const int X = x + g.gx, Y = y + kGY;
-    int X2 = -1, Y2 = -1;
-    if (x < 3) X2 = X + g.nx;
-    else if (x >= g.nx - 3) X2 = X - g.nx;
-    if (g.periodic) {
-        if (y < 3) Y2 = Y + g.ny;
-        else if (y >= g.ny - 3) Y2 = Y - g.ny;
-    }
-    pl[(long long)Y * g.pitch + X] = v;
-    if (X2 >= 0) pl[(long long)Y * g.pitch + X2] = v;
-    if (Y2 >= 0) {
-        pl[(long long)Y2 * g.pitch + X] = v;
-        if (X2 >= 0) pl[(long long)Y2 * g.pitch + X2] = v;
+// Pair (A, B) of plane i at site (x, y) in the padded global buffer, in
+// units of pairs: row stride `pitch`, plane stride rows * pitch.
+template <typename T2>
+__device__ __forceinline__ void put2(T2* base, const Geom& g, int i, int x, int y, T2 v) {
+    const long long pl = (long long)g.rows * g.pitch;
+    T2* p = base + i * pl + (long long)(y + kGY) * g.pitch + (x + g.gx);
+    const int dX = (x < 3) ? g.nx : ((x >= g.nx - 3) ? -g.nx : 0);
+    long long dY = 0;
+    if (g.periodic) dY = (y < 3) ? (long long)g.ny * g.pitch : ((y >= g.ny - 3) ? -(long long)g.ny * g.pitch : 0);
+    p[0] = v;
+    if (dX) p[dX] = v;
+    if (dY) {
+        p[dY] = v;
+        if (dX) p[dY + dX] = v;
     }
 }
 
-// The offsets h_i(r, t) = f_i(r, t) - w_i rho_ref of one species at lattice
-// site (x, y), whose box coordinates are (sx, sy).  pull = 1: streamed from
-// h*(r - c_i, t - 1), with halfway bounce-back at the Couette walls:
-// f_i = f*_opp(i)(r) + 6 w_i rho_w (c_i . u_w), where rho_w is the
-// pre-streaming density of the boundary node, rho_ref + sum_j h*_j(r).
+template <typename C>
+__device__ __forceinline__ C sum9(const C h[9]) {
+    return ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
+}
+
+// The offsets h_i(r, t) of both species at lattice site (x, y), whose box
+// coordinates are (sx, sy).  pull = 1: streamed from h*(r - c_i, t - 1), with
+// halfway bounce-back at the Couette walls: f_i = f*_opp(i)(r)
+// + 6 w_i rho_w (c_i . u_w), rho_w the pre-streaming density of the
+// boundary node, rho_ref + sum_j h*_j(r).
 template <int P, bool PER>
-__device__ __forceinline__ void load_site(const typename Prec<P>::T* sf, int sx, int sy, int y,
+__device__ __forceinline__ void load_site(const typename Prec<P>::T2* box, int sx, int sy, int y,
                                           const StepArgs<typename Prec<P>::C>& a,
-                                          typename Prec<P>::C h[9]) {
+                                          typename Prec<P>::C hA[9], typename Prec<P>::C hB[9]) {
     typedef Layout<P> L;
     typedef typename Prec<P>::C C;
+    typedef typename Prec<P>::C2 C2;
     if (a.pull) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) h[i] = dec(sf[(i * L::BY + sy - cy(i)) * L::BX + sx - cx(i)]);
+        for (int i = 0; i < 9; ++i) {
+            const C2 v = dec2(box[(i * L::BY + sy - cy(i)) * L::BX + sx - cx(i)]);
+            hA[i] = v.x;
+            hB[i] = v.y;
+        }
         if (!PER && (y == 0 || y == a.g.ny - 1)) {
-            C dr = C(0);
+            C sA[9], sB[9];
 #pragma unroll
-            for (int j = 0; j < 9; ++j) dr += dec(sf[(j * L::BY + sy) * L::BX + sx]);
-            const C rw = a.k.rho_ref + dr;
+            for (int j = 0; j < 9; ++j) {
+                const C2 v = dec2(box[(j * L::BY + sy) * L::BX + sx]);
+                sA[j] = v.x;
+                sB[j] = v.y;
+            }
+            const C rwA = a.k.rho_ref + sum9(sA), rwB = a.k.rho_ref + sum9(sB);
             const int up = (y == 0);                 // links arriving upward
             const C uw = up ? -a.k.u_wall : a.k.u_wall;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                if ((up && cy(i) == 1) || (!up && cy(i) == -1))
-                    h[i] = dec(sf[(opp(i) * L::BY + sy) * L::BX + sx]) +
-                           C(6) * wgt<C>(i) * rw * (C(cx(i)) * uw);
+                if ((up && cy(i) == 1) || (!up && cy(i) == -1)) {
+                    const C m = C(6) * wgt<C>(i) * (C(cx(i)) * uw);
+                    hA[i] = sA[opp(i)] + m * rwA;
+                    hB[i] = sB[opp(i)] + m * rwB;
+                }
             }
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) h[i] = dec(sf[(i * L::BY + sy) * L::BX + sx]);
+        for (int i = 0; i < 9; ++i) {
+            const C2 v = dec2(box[(i * L::BY + sy) * L::BX + sx]);
+            hA[i] = v.x;
+            hB[i] = v.y;
+        }
     }
 }
 
@@ -170,46 +186,74 @@ __device__ __forceinline__ C dpsi_of(C d, const Coef<C>& k) {
     return -k.psi_scale * cexpm1(-d * k.inv_rho0);
 }
 
+// Post-collision offsets of one species (Eq. (1), BGK toward the
+// equilibrium at velocity (ux, uy)):
+// h*_i = h_i + omega (heq_i - h_i) [+ 3 w_i c_i . F for the source scheme],
+// heq_i = f^eq_i - w_i rho_ref = w_i [d_rho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u^2)],
+// evaluated per pair (i, opp(i)), whose c.u differ only in sign:
+// heq = E +- O with E = w (d_rho - 1.5 rho u^2 + 4.5 rho (c.u)^2), O = 3 w rho c.u.
+template <typename C, bool SRC>
+__device__ __forceinline__ void collide(const C h[9], C out[9], C drho, C rho, C ux, C uy,
+                                        C om, C Fx, C Fy) {
+    const C Q = drho - rho * (C(1.5) * (ux * ux + uy * uy));
+    out[0] = h[0] + om * (wgt<C>(0) * Q - h[0]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int i = k == 0 ? 1 : (k == 1 ? 2 : (k == 2 ? 5 : 6));   // c.u = ux, uy, ux+uy, uy-ux
+        const int j = opp(i);
+        const C cu = C(cx(i)) * ux + C(cy(i)) * uy;
+        const C w = wgt<C>(i);
+        const C rcu = rho * cu;
+        const C E = w * (Q + C(4.5) * cu * rcu);
+        const C O = (C(3) * w) * rcu;
+        out[i] = h[i] + om * ((E + O) - h[i]);
+        out[j] = h[j] + om * ((E - O) - h[j]);
+        if (SRC) {
+            const C S = (C(3) * w) * (C(cx(i)) * Fx + C(cy(i)) * Fy);
+            out[i] += S;
+            out[j] -= S;
+        }
+    }
+}
+
 // ------------------------------------------------------------- tile body
-// Phases 2-3 for one TX x TY tile whose f* box (tile + 3-cell halo, both
-// species) is in shared memory.  One site per thread in phase 3.
+// Phases 2-3 for one TX x TY tile whose f* box is in shared memory.
 // OBS = false: collision and write-back of f*(t) (+ wall momentum into red).
 // OBS = true : fields / populations / totals of the current state (red =
 //              mass_A, mass_B, mom_x, mom_y).
 // V: bit 0 = periodic in y (else Couette walls); bit 1 = general forcing
 // (additive source term or body acceleration checked at run time).
 template <int P, bool OBS, int V>
-__device__ __forceinline__ void tile_body(const typename Prec<P>::T* __restrict__ sfA,
-                                          const typename Prec<P>::T* __restrict__ sfB,
-                                          typename Prec<P>::C* __restrict__ srho,
-                                          typename Prec<P>::C* __restrict__ spsi, int x0, int y0,
+__device__ __forceinline__ void tile_body(const typename Prec<P>::T2* __restrict__ box,
+                                          typename Prec<P>::C2* __restrict__ srho,
+                                          typename Prec<P>::C2* __restrict__ spsi, int x0, int y0,
                                           const StepArgs<typename Prec<P>::C>& a, double red[4],
-                                          bool& bad, typename Prec<P>::T* __restrict__ stage) {
+                                          bool& bad, typename Prec<P>::T2* __restrict__ stage) {
     typedef Layout<P> L;
-    typedef typename L::T T;
+    typedef typename L::T2 T2;
     typedef typename L::C C;
+    typedef typename L::C2 C2;
     constexpr bool PER = (V & 1) != 0;
     constexpr bool GEN = (V & 2) != 0;
     const int tid = threadIdx.x;
     const Geom& g = a.g;
 
     // 2. density and pseudo-potential deviations d_rho = rho - rho_ref,
-    // d_Psi = Psi(rho) - Psi(rho_ref) on the tile + 2-cell halo.
+    // d_Psi = Psi(rho) - Psi(rho_ref), on the tile + 2-cell halo.
     for (int c = tid; c < L::RX * L::RY; c += L::NT) {
         const int ly = c / L::RX, lx = c - ly * L::RX;
         const int y = y0 - 2 + ly;
         if (!PER && (y < 0 || y >= g.ny)) continue;
-        const int sx = lx - 2 + L::GX, sy = ly - 2 + kGY;
-        C h[9];
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            load_site<P, PER>(s ? sfB : sfA, sx, sy, y, a, h);
-            C r = C(0);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) r += h[i];
-            srho[(s * L::RY + ly) * L::RX + lx] = r;
-            spsi[(s * L::RY + ly) * L::RX + lx] = dpsi_of(r, a.k);
-        }
+        C hA[9], hB[9];
+        load_site<P, PER>(box, lx - 2 + L::GX, ly - 2 + kGY, y, a, hA, hB);
+        const C rA = sum9(hA), rB = sum9(hB);
+        C2 r, q;
+        r.x = rA;
+        r.y = rB;
+        q.x = dpsi_of(rA, a.k);
+        q.y = dpsi_of(rB, a.k);
+        srho[ly * L::RX + lx] = r;
+        spsi[ly * L::RX + lx] = q;
     }
     if (!PER) {   // mirror the deviations about the halfway walls
         __syncthreads();
@@ -222,11 +266,8 @@ __device__ __forceinline__ void tile_body(const typename Prec<P>::T* __restrict_
             else continue;
             const int lm = ym - (y0 - 2);
             if (lm < 0 || lm >= L::RY) continue;
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                srho[(s * L::RY + ly) * L::RX + lx] = srho[(s * L::RY + lm) * L::RX + lx];
-                spsi[(s * L::RY + ly) * L::RX + lx] = spsi[(s * L::RY + lm) * L::RX + lx];
-            }
+            srho[ly * L::RX + lx] = srho[lm * L::RX + lx];
+            spsi[ly * L::RX + lx] = spsi[lm * L::RX + lx];
         }
     }
     // the previous tile's bulk store must have read the staging tile
@@ -237,55 +278,67 @@ __device__ __forceinline__ void tile_body(const typename Prec<P>::T* __restrict_
     const int lx = tid % L::TX, ly = tid / L::TX;
     const int x = x0 + lx, y = y0 + ly;
     if (x >= g.nx || y >= g.ny) return;
-    const int sx = lx + L::GX, sy = ly + kGY;
-    const int rx = lx + 2, ry = ly + 2;
     C h[2][9];
-    load_site<P, PER>(sfA, sx, sy, y, a, h[0]);
-    load_site<P, PER>(sfB, sx, sy, y, a, h[1]);
+    load_site<P, PER>(box, lx + L::GX, ly + kGY, y, a, h[0], h[1]);
     C drho[2], rho[2], jx[2], jy[2];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-        C r = C(0), mx = C(0), my = C(0);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) r += h[s][i];
+        drho[s] = sum9(h[s]);
+        rho[s] = a.k.rho_ref + drho[s];
         // sum_i w_i c_i = 0, so the offsets carry all of j
-        mx = (h[s][1] - h[s][3]) + ((h[s][5] - h[s][7]) + (h[s][8] - h[s][6]));
-        my = (h[s][2] - h[s][4]) + ((h[s][5] - h[s][7]) + (h[s][6] - h[s][8]));
-        drho[s] = r;
-        rho[s] = a.k.rho_ref + r;
-        jx[s] = mx;
-        jy[s] = my;
+        const C d57 = h[s][5] - h[s][7], d68 = h[s][6] - h[s][8];
+        jx[s] = (h[s][1] - h[s][3]) + (d57 - d68);
+        jy[s] = (h[s][2] - h[s][4]) + (d57 + d68);
     }
     if (!(isfinite(rho[0]) && isfinite(rho[1]))) bad = true;
 
     // Eq. (2): F_s = -Psi_s(r) sum_d K_s(d) d [Psi_s(r+d) - Psi_s(r-d)]
     //               - (G_X/rho0) rho_s(r) sum_d w(d) d [rho_s'(r+d) - rho_s'(r-d)]
-    // (the reference values cancel in the differences).
-    C Fx[2], Fy[2];
+    // over one representative d of each +-d pair (the reference values cancel
+    // in the differences); belt-1 and belt-2 pairs accumulate separately.
+    const int c0 = (ly + 2) * L::RX + (lx + 2);
+    C axA1 = C(0), ayA1 = C(0), axB1 = C(0), ayB1 = C(0);
+    C axA2 = C(0), ayA2 = C(0), axB2 = C(0), ayB2 = C(0);
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        const C* ps = spsi + s * L::RX * L::RY + ry * L::RX + rx;
-        const C* ro = srho + (1 - s) * L::RX * L::RY + ry * L::RX + rx;
-        C ax = C(0), ay = C(0);
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            const int dx = rdx(k), dy = rdy(k);
-            const C diff = ps[dy * L::RX + dx] - ps[-dy * L::RX - dx];
-            if (dx != 0) ax += (a.k.K[s][k] * C(dx)) * diff;
-            if (dy != 0) ay += (a.k.K[s][k] * C(dy)) * diff;
+    for (int k = 0; k < 12; ++k) {
+        const int dx = rdx(k), dy = rdy(k);
+        const C2 pp = spsi[c0 + dy * L::RX + dx], pm = spsi[c0 - dy * L::RX - dx];
+        const C dA = pp.x - pm.x, dB = pp.y - pm.y;
+        C& axA = k < 4 ? axA1 : axA2;
+        C& ayA = k < 4 ? ayA1 : ayA2;
+        C& axB = k < 4 ? axB1 : axB2;
+        C& ayB = k < 4 ? ayB1 : ayB2;
+        if (dx != 0) {
+            axA += (a.k.K[0][k] * C(dx)) * dA;
+            axB += (a.k.K[1][k] * C(dx)) * dB;
         }
-        C qx = C(0), qy = C(0);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int dx = rdx(k), dy = rdy(k);
-            const C diff = ro[dy * L::RX + dx] - ro[-dy * L::RX - dx];
-            if (dx != 0) qx += (a.k.W[k] * C(dx)) * diff;
-            if (dy != 0) qy += (a.k.W[k] * C(dy)) * diff;
+        if (dy != 0) {
+            ayA += (a.k.K[0][k] * C(dy)) * dA;
+            ayB += (a.k.K[1][k] * C(dy)) * dB;
         }
-        const C pc = a.k.psi_ref + ps[0];
-        Fx[s] = -pc * ax - a.k.gx_rho0 * rho[s] * qx;
-        Fy[s] = -pc * ay - a.k.gx_rho0 * rho[s] * qy;
     }
+    C qxA = C(0), qyA = C(0), qxB = C(0), qyB = C(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int dx = rdx(k), dy = rdy(k);
+        const C2 rp = srho[c0 + dy * L::RX + dx], rm = srho[c0 - dy * L::RX - dx];
+        const C dB = rp.y - rm.y, dA = rp.x - rm.x;   // A feels rho_B, B feels rho_A
+        if (dx != 0) {
+            qxA += (a.k.W[k] * C(dx)) * dB;
+            qxB += (a.k.W[k] * C(dx)) * dA;
+        }
+        if (dy != 0) {
+            qyA += (a.k.W[k] * C(dy)) * dB;
+            qyB += (a.k.W[k] * C(dy)) * dA;
+        }
+    }
+    const C2 pc = spsi[c0];
+    const C pcA = a.k.psi_ref + pc.x, pcB = a.k.psi_ref + pc.y;
+    C Fx[2], Fy[2];
+    Fx[0] = -pcA * (axA1 + axA2) - a.k.gx_rho0 * rho[0] * qxA;
+    Fy[0] = -pcA * (ayA1 + ayA2) - a.k.gx_rho0 * rho[0] * qyA;
+    Fx[1] = -pcB * (axB1 + axB2) - a.k.gx_rho0 * rho[1] * qxB;
+    Fy[1] = -pcB * (ayB1 + ayB2) - a.k.gx_rho0 * rho[1] * qyB;
     if (GEN && a.k.has_accel) {
         C acc = a.k.g_x;
         if (a.k.kolmo_amp != C(0)) acc += a.k.kolmo_amp * csin(a.k.kolmo_w * C(y));
@@ -320,9 +373,8 @@ __device__ __forceinline__ void tile_body(const typename Prec<P>::T* __restrict_
         return;
     }
 
-    // Eq. (1): forced BGK relaxation of the offsets,
-    // h*_i = h_i + omega (heq_i - h_i), heq_i = f^eq_i - w_i rho_ref
-    //      = w_i [d_rho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u^2)].
+    // Eq. (1): forced BGK relaxation.  Common velocity
+    // u' = sum_s (j_s/tau_s) / sum_s (rho_s/tau_s); shift u_s = u' + tau_s F_s/rho_s.
     const C den = rho[0] * a.k.omega[0] + rho[1] * a.k.omega[1];
     C upx = C(0), upy = C(0);
     if (den != C(0)) {
@@ -330,17 +382,8 @@ __device__ __forceinline__ void tile_body(const typename Prec<P>::T* __restrict_
         upx = (jx[0] * a.k.omega[0] + jx[1] * a.k.omega[1]) * inv;
         upy = (jy[0] * a.k.omega[0] + jy[1] * a.k.omega[1]) * inv;
     }
-    // Store address of plane 0 at (x, y) and the periodic ghost copies.
-    T* __restrict__ out = reinterpret_cast<T*>(a.fout) + (long long)(y + kGY) * g.pitch + (x + g.gx);
-    const long long PL = g.plane;
-    const int dX = (x < 3) ? g.nx : ((x >= g.nx - 3) ? -g.nx : 0);
-    long long dY = 0;
-    if (PER) dY = (y < 3) ? (long long)g.ny * g.pitch : ((y >= g.ny - 3) ? -(long long)g.ny * g.pitch : 0);
-    const bool ghost = (dX != 0) || (dY != 0);
-    const bool wall = !PER && (y == 0 || y == g.ny - 1);
-    // Full tiles go through the staging tile and a bulk tensor store.
-    const bool staged = stage != nullptr && x0 + L::TX <= g.nx && y0 + L::TY <= g.ny;
     const bool source = GEN && a.k.source;
+    C hs[2][9];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         C ux = upx, uy = upy;
@@ -349,51 +392,61 @@ __device__ __forceinline__ void tile_body(const typename Prec<P>::T* __restrict_
             ux += tr * Fx[s];
             uy += tr * Fy[s];
         }
-        const C usq = C(1.5) * (ux * ux + uy * uy);
-        const C om = a.k.omega[s];
-        T e[9];
+        if (source)
+            collide<C, true>(h[s], hs[s], drho[s], rho[s], ux, uy, a.k.omega[s], Fx[s], Fy[s]);
+        else
+            collide<C, false>(h[s], hs[s], drho[s], rho[s], ux, uy, a.k.omega[s], Fx[s], Fy[s]);
+    }
+    T2 e[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) e[i] = enc2<T2, C>(hs[0][i], hs[1][i]);
+
+    // Full tiles go through the staging tile and a bulk tensor store; ragged
+    // tiles and periodic ghost copies use plain stores.
+    const bool staged = stage != nullptr && x0 + L::TX <= g.nx && y0 + L::TY <= g.ny;
+    const int dX = (x < 3) ? g.nx : ((x >= g.nx - 3) ? -g.nx : 0);
+    long long dY = 0;
+    if (PER) dY = (y < 3) ? (long long)g.ny * g.pitch : ((y >= g.ny - 3) ? -(long long)g.ny * g.pitch : 0);
+    if (staged) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) stage[(i * L::TY + ly) * L::TX + lx] = e[i];
+    }
+    if (!staged || dX != 0 || dY != 0) {
+        const long long PL = (long long)g.rows * g.pitch;
+        T2* __restrict__ out =
+            reinterpret_cast<T2*>(a.fout) + (long long)(y + kGY) * g.pitch + (x + g.gx);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const C cu = C(cx(i)) * ux + C(cy(i)) * uy;
-            const C heq = wgt<C>(i) * (drho[s] + rho[s] * (cu * (C(3) + C(4.5) * cu) - usq));
-            C v = h[s][i] + om * (heq - h[s][i]);
-            if (source) v += wgt<C>(i) * C(3) * (C(cx(i)) * Fx[s] + C(cy(i)) * Fy[s]);
-            e[i] = encf<T>(v);
-            if (staged)
-                stage[((s * 9 + i) * L::TY + ly) * L::TX + lx] = e[i];
-            else
-                out[(s * 9 + i) * PL] = e[i];
-        }
-        if (ghost) {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                T* o = out + (s * 9 + i) * PL;
-                if (dX) o[dX] = e[i];
-                if (dY) {
-                    o[dY] = e[i];
-                    if (dX) o[dY + dX] = e[i];
-                }
+            T2* o = out + i * PL;
+            if (!staged) o[0] = e[i];
+            if (dX) o[dX] = e[i];
+            if (dY) {
+                o[dY] = e[i];
+                if (dX) o[dY + dX] = e[i];
             }
         }
-        if (wall) {
-            // x-momentum handed to the wall by the links that will bounce
-            // back at the next streaming: c_x (f*_i + f_opp),
-            // f_opp = f*_i - 6 w_i rho_w (c_i . u_w).
-            const int down = (y == 0);
-            const C uw = down ? -a.k.u_wall : a.k.u_wall;
-            C hs[9];
-            C dr = C(0);
+    }
+    if (!PER && (y == 0 || y == g.ny - 1)) {
+        // x-momentum handed to the wall by the links that will bounce back
+        // at the next streaming: c_x (f*_i + f_opp), f_opp = f*_i - 6 w_i
+        // rho_w (c_i . u_w), from the stored (rounded) values.
+        const int down = (y == 0);
+        const C uw = down ? -a.k.u_wall : a.k.u_wall;
+        C sA[9], sB[9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                hs[i] = dec(e[i]);
-                dr += hs[i];
-            }
-            const C rw = a.k.rho_ref + dr;
+        for (int i = 0; i < 9; ++i) {
+            const C2 v = dec2(e[i]);
+            sA[i] = v.x;
+            sB[i] = v.y;
+        }
+        const C rw[2] = {a.k.rho_ref + sum9(sA), a.k.rho_ref + sum9(sB)};
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                if ((down && cy(i) == -1) || (!down && cy(i) == 1)) {
-                    const C fi = hs[i] + wgt<C>(i) * a.k.rho_ref;
-                    const C back = fi - C(6) * wgt<C>(i) * rw * (C(cx(i)) * uw);
+        for (int i = 0; i < 9; ++i) {
+            if ((down && cy(i) == -1) || (!down && cy(i) == 1)) {
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    const C fi = (s ? sB[i] : sA[i]) + wgt<C>(i) * a.k.rho_ref;
+                    const C back = fi - C(6) * wgt<C>(i) * rw[s] * (C(cx(i)) * uw);
                     const double dp = (double)(C(cx(i)) * (fi + back));
                     if (down) red[0] += dp; else red[1] += dp;
                 }
@@ -428,9 +481,9 @@ __device__ __forceinline__ void block_sum4(double red[4], double (*s_red)[4]) {
 // arrives last sums the `nslots` slots of `width` doubles in a fixed order.
 // Returns true in the last CTA, with the sums in red (valid in thread 0).
 template <int NT>
-__device__ __forceinline__ bool last_cta_sum(DevStats* st,
-                                             const double* slots, int nslots, int width,
-                                             double red[4], double (*s_red)[4], int* s_last) {
+__device__ __forceinline__ bool last_cta_sum(DevStats* st, const double* slots, int nslots,
+                                             int width, double red[4], double (*s_red)[4],
+                                             int* s_last) {
     const int tid = threadIdx.x;
     if (tid == 0) {
         __threadfence();
@@ -455,23 +508,22 @@ __device__ __forceinline__ bool last_cta_sum(DevStats* st,
 // (row-major tile order, so the CTAs in flight cover a narrow band of rows and
 // the halo overlap between tile rows is served by L2).  The box of the next
 // tile is loaded by TMA into the second buffer while the current tile is
-// computed.
+// computed; full tiles are written back by bulk tensor stores.
 template <int P, int V>
 __global__ void __launch_bounds__(Layout<P>::NT, 1)
     k_step(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
            const __grid_constant__ StepArgs<typename Prec<P>::C> a) {
     typedef Layout<P> L;
-    typedef typename L::T T;
-    typedef typename L::C C;
+    typedef typename L::T2 T2;
+    typedef typename L::C2 C2;
     extern __shared__ unsigned char smem_raw[];
     // 128-byte aligned base, derived from the shared array by indexing so
     // that every access below compiles to shared-memory instructions.
     unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    // box b (b = 0, 1) holds both species: A at +0, B at +SPEC_STRIDE bytes
-    auto box = [&](int b) { return reinterpret_cast<T*>(smem + b * (2 * L::SPEC_STRIDE)); };
-    C* srho = reinterpret_cast<C*>(smem + 4 * L::SPEC_STRIDE);   // [2][RY][RX]
-    C* spsi = srho + 2 * L::RX * L::RY;                           // [2][RY][RX]
-    T* stage = reinterpret_cast<T*>(smem + L::STAGE_OFF);         // [18][TY][TX]
+    auto box = [&](int b) { return reinterpret_cast<T2*>(smem + b * L::BOX_STRIDE); };
+    C2* srho = reinterpret_cast<C2*>(smem + 2 * L::BOX_STRIDE);   // [RY][RX]
+    C2* spsi = srho + L::RX * L::RY;                              // [RY][RX]
+    T2* stage = reinterpret_cast<T2*>(smem + L::STAGE_OFF);       // [9][TY][TX]
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ int s_fail, s_last;
     __shared__ double s_red[L::NT / 32][4];
@@ -488,13 +540,12 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
         fence_mbar_init();
     }
     __syncthreads();
-    // Box origin in padded coordinates: column x0 (= x0 - gx + gx), row y0
-    // (= y0 - 3 + kGY).
+    // Box origin in padded coordinates: site column x0 (= x0 - gx + gx), i.e.
+    // element 2 x0 of the interleaved rows, and row y0 (= y0 - 3 + kGY).
     auto issue = [&](int tile, int b) {
         const int x0 = (tile % ntx) * L::TX, y0 = (tile / ntx) * L::TY;
-        mbar_expect_tx(&bars[b], 2u * L::SPEC_BYTES);
-        tma_load_3d(box(b), &tin, x0, y0, 0, &bars[b]);
-        tma_load_3d(box(b) + L::SPEC_STRIDE / sizeof(T), &tin, x0, y0, 9, &bars[b]);
+        mbar_expect_tx(&bars[b], (uint32_t)L::BOX_BYTES);
+        tma_load_3d(box(b), &tin, 2 * x0, y0, 0, &bars[b]);
     };
     if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
 
@@ -504,20 +555,18 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
         const int b = k & 1;
         if (tid == 0 && tile + (int)gridDim.x < ntiles) {
-            fence_proxy_async();   // earlier generic reads of box[b^1] before the async write
+            fence_proxy_async();   // earlier generic reads of box b^1 before the async write
             issue(tile + gridDim.x, b ^ 1);
         }
         if (!mbar_wait_bounded(&bars[b], (k >> 1) & 1)) s_fail = 1;
         __syncthreads();
         if (s_fail) break;
         const int x0 = (tile % ntx) * L::TX, y0 = (tile / ntx) * L::TY;
-        tile_body<P, false, V>(box(b), box(b) + L::SPEC_STRIDE / sizeof(T), srho, spsi, x0, y0,
-                               a, red, bad, stage);
+        tile_body<P, false, V>(box(b), srho, spsi, x0, y0, a, red, bad, stage);
         __syncthreads();
         if (tid == 0 && x0 + L::TX <= g.nx && y0 + L::TY <= g.ny) {
-            // padded coordinates of site (x0, y0): column x0 + gx, row y0 + kGY
-            tma_store_3d(&tout, stage, x0 + L::GX, y0 + kGY, 0);
-            tma_store_3d(&tout, stage + L::STAGE_SPEC / sizeof(T), x0 + L::GX, y0 + kGY, 9);
+            // padded coordinates of site (x0, y0): pair column x0 + gx, row y0 + kGY
+            tma_store_3d(&tout, stage, 2 * (x0 + L::GX), y0 + kGY, 0);
             bulk_commit();
         }
     }
@@ -561,15 +610,13 @@ __global__ void __launch_bounds__(Layout<P>::NT)
     k_observe(const __grid_constant__ CUtensorMap tin,
               const __grid_constant__ StepArgs<typename Prec<P>::C> a) {
     typedef Layout<P> L;
-    typedef typename L::T T;
-    typedef typename L::C C;
+    typedef typename L::T2 T2;
+    typedef typename L::C2 C2;
     extern __shared__ unsigned char smem_raw[];
-    // 128-byte aligned base, derived from the shared array by indexing so
-    // that every access below compiles to shared-memory instructions.
     unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    T* sfA = reinterpret_cast<T*>(smem);
-    C* srho = reinterpret_cast<C*>(smem + 2 * L::SPEC_STRIDE);
-    C* spsi = srho + 2 * L::RX * L::RY;
+    T2* box = reinterpret_cast<T2*>(smem);
+    C2* srho = reinterpret_cast<C2*>(smem + L::BOX_STRIDE);
+    C2* spsi = srho + L::RX * L::RY;
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_fail, s_last;
     __shared__ double s_red[L::NT / 32][4];
@@ -579,9 +626,8 @@ __global__ void __launch_bounds__(Layout<P>::NT)
         s_fail = 0;
         mbar_init(&bar, 1);
         fence_mbar_init();
-        mbar_expect_tx(&bar, 2u * L::SPEC_BYTES);
-        tma_load_3d(sfA, &tin, x0, y0, 0, &bar);
-        tma_load_3d(sfA + L::SPEC_STRIDE / sizeof(T), &tin, x0, y0, 9, &bar);
+        mbar_expect_tx(&bar, (uint32_t)L::BOX_BYTES);
+        tma_load_3d(box, &tin, 2 * x0, y0, 0, &bar);
     }
     __syncthreads();
     if (!mbar_wait_bounded(&bar, 0)) s_fail = 1;
@@ -589,8 +635,7 @@ __global__ void __launch_bounds__(Layout<P>::NT)
     double red[4] = {0.0, 0.0, 0.0, 0.0};
     bool bad = false;
     if (!s_fail) {
-        tile_body<P, true, V>(sfA, sfA + L::SPEC_STRIDE / sizeof(T), srho, spsi, x0, y0, a, red,
-                              bad, nullptr);
+        tile_body<P, true, V>(box, srho, spsi, x0, y0, a, red, bad, nullptr);
     } else if (tid == 0) {
         atomicOr(&a.st->err, ERR_TIMEOUT);
         mbar_wait_bounded(&bar, 0);
@@ -615,10 +660,10 @@ __global__ void __launch_bounds__(Layout<P>::NT)
 // f(r, 0) = f^eq(rho_s, u) in place (the first step reads it unshifted).
 // mode 0: rho_s from the counter generator; mode 1: FP64 fields [4][ny][nx].
 template <int P>
-__global__ void k_init(Geom g, Coef<typename Prec<P>::C> k, typename Prec<P>::T* fout, int mode,
+__global__ void k_init(Geom g, Coef<typename Prec<P>::C> k, typename Prec<P>::T2* fout, int mode,
                        const double* fields, double rho0, double amp, double u_wall, int init_shear,
                        unsigned long long seed) {
-    typedef typename Prec<P>::T T;
+    typedef typename Prec<P>::T2 T2;
     const long long N = (long long)g.nx * g.ny;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
          idx += (long long)gridDim.x * blockDim.x) {
@@ -641,14 +686,15 @@ __global__ void k_init(Geom g, Coef<typename Prec<P>::C> k, typename Prec<P>::T*
         }
         const double usq = ux * ux + uy * uy;
         const double rref = (double)k.rho_ref;
-        for (int s = 0; s < 2; ++s)
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const double cu = cx(i) * ux + cy(i) * uy;
-                // f^eq_i - w_i rho_ref
-                const double h = wgt<double>(i) * ((r[s] - rref) + r[s] * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq));
-                put<T>(fout, g, s * 9 + i, x, y, encd<T>(h));
-            }
+        for (int i = 0; i < 9; ++i) {
+            const double cu = cx(i) * ux + cy(i) * uy;
+            const double e = 3.0 * cu + 4.5 * cu * cu - 1.5 * usq;
+            // f^eq_i - w_i rho_ref for both species
+            const double hA = wgt<double>(i) * ((r[0] - rref) + r[0] * e);
+            const double hB = wgt<double>(i) * ((r[1] - rref) + r[1] * e);
+            put2<T2>(fout, g, i, x, y, encd2<T2>(hA, hB));
+        }
     }
 }
 
@@ -700,12 +746,12 @@ cudaError_t launch_init_prec(const Geom& g, const void* coef, void* fout, int mo
                              const double* fields, double rho0, double amp, double u_wall,
                              int init_shear, unsigned long long seed, cudaStream_t s) {
     typedef typename Prec<P>::C C;
-    typedef typename Prec<P>::T T;
+    typedef typename Prec<P>::T2 T2;
     const long long N = (long long)g.nx * g.ny;
     long long blocks = (N + 255) / 256;
     if (blocks > 152 * 64) blocks = 152 * 64;
     k_init<P><<<(unsigned)blocks, 256, 0, s>>>(g, *reinterpret_cast<const Coef<C>*>(coef),
-                                               reinterpret_cast<T*>(fout), mode, fields, rho0, amp,
+                                               reinterpret_cast<T2*>(fout), mode, fields, rho0, amp,
                                                u_wall, init_shear, seed);
     return cudaGetLastError();
 }

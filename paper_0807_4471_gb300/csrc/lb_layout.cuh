@@ -37,46 +37,60 @@ __host__ __device__ constexpr int rdy(int k) {
 }
 
 // ------------------------------------------------------- storage formats
+// In HBM and in shared memory the two species of one direction are stored
+// as an interleaved pair (A, B), so that one vector access serves both.
+// T: stored scalar, T2: stored pair, C: compute scalar, C2: compute pair.
 template <int P> struct Prec;
 template <> struct Prec<LB_FP64> {
-    typedef double T; typedef double C;
+    typedef double T; typedef double2 T2; typedef double C; typedef double2 C2;
     static constexpr int GX = 4, TX = 32, TY = 8;
 };
 template <> struct Prec<LB_FP32> {
-    typedef float T; typedef float C;
+    typedef float T; typedef float2 T2; typedef float C; typedef float2 C2;
     static constexpr int GX = 4, TX = 64, TY = 8;
 };
 template <> struct Prec<LB_FP16_OFFSET> {
-    typedef __half T; typedef float C;
+    typedef __half T; typedef __half2 T2; typedef float C; typedef float2 C2;
     static constexpr int GX = 8, TX = 64, TY = 8;
 };
 template <> struct Prec<LB_BF16_OFFSET> {
-    typedef __nv_bfloat16 T; typedef float C;
+    typedef __nv_bfloat16 T; typedef __nv_bfloat162 T2; typedef float C; typedef float2 C2;
     static constexpr int GX = 8, TX = 64, TY = 8;
 };
 
 // Stored values are offsets h_i = f_i - w_i rho_ref from the lattice weights
 // (all precisions).  The codecs only convert between storage and compute type.
-__device__ __forceinline__ double dec(double v) { return v; }
-__device__ __forceinline__ float dec(float v) { return v; }
-__device__ __forceinline__ float dec(__half v) { return __half2float(v); }
-__device__ __forceinline__ float dec(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ double2 dec2(double2 v) { return v; }
+__device__ __forceinline__ float2 dec2(float2 v) { return v; }
+__device__ __forceinline__ float2 dec2(__half2 v) { return __half22float2(v); }
+__device__ __forceinline__ float2 dec2(__nv_bfloat162 v) { return __bfloat1622float2(v); }
 
-template <typename T> __device__ __forceinline__ T encf(double v);
-template <> __device__ __forceinline__ double encf<double>(double v) { return v; }
-template <typename T> __device__ __forceinline__ T encf(float v);
-template <> __device__ __forceinline__ float encf<float>(float v) { return v; }
-template <> __device__ __forceinline__ __half encf<__half>(float v) { return __float2half_rn(v); }
-template <> __device__ __forceinline__ __nv_bfloat16 encf<__nv_bfloat16>(float v) {
-    return __float2bfloat16_rn(v);
+template <typename T2, typename C> __device__ __forceinline__ T2 enc2(C a, C b);
+template <> __device__ __forceinline__ double2 enc2<double2, double>(double a, double b) {
+    return make_double2(a, b);
 }
-// Encoding of an offset computed in double (initialisation).
-template <typename T> __device__ __forceinline__ T encd(double v);
-template <> __device__ __forceinline__ double encd<double>(double v) { return v; }
-template <> __device__ __forceinline__ float encd<float>(double v) { return (float)v; }
-template <> __device__ __forceinline__ __half encd<__half>(double v) { return __double2half(v); }
-template <> __device__ __forceinline__ __nv_bfloat16 encd<__nv_bfloat16>(double v) {
-    return __double2bfloat16(v);
+template <> __device__ __forceinline__ float2 enc2<float2, float>(float a, float b) {
+    return make_float2(a, b);
+}
+template <> __device__ __forceinline__ __half2 enc2<__half2, float>(float a, float b) {
+    return __floats2half2_rn(a, b);
+}
+template <> __device__ __forceinline__ __nv_bfloat162 enc2<__nv_bfloat162, float>(float a, float b) {
+    return __floats2bfloat162_rn(a, b);
+}
+// Encoding of offsets computed in double (initialisation).
+template <typename T2> __device__ __forceinline__ T2 encd2(double a, double b);
+template <> __device__ __forceinline__ double2 encd2<double2>(double a, double b) {
+    return make_double2(a, b);
+}
+template <> __device__ __forceinline__ float2 encd2<float2>(double a, double b) {
+    return make_float2((float)a, (float)b);
+}
+template <> __device__ __forceinline__ __half2 encd2<__half2>(double a, double b) {
+    return __halves2half2(__double2half(a), __double2half(b));
+}
+template <> __device__ __forceinline__ __nv_bfloat162 encd2<__nv_bfloat162>(double a, double b) {
+    return __halves2bfloat162(__double2bfloat16(a), __double2bfloat16(b));
 }
 
 // Correctly rounded reciprocal (no division slow path in FP32).
@@ -91,22 +105,24 @@ __device__ __forceinline__ float csin(float v) { return sinf(v); }
 template <int P>
 struct Layout {
     typedef typename Prec<P>::T T;
+    typedef typename Prec<P>::T2 T2;
     typedef typename Prec<P>::C C;
+    typedef typename Prec<P>::C2 C2;
     static constexpr int TX = Prec<P>::TX, TY = Prec<P>::TY, NT = TX * TY;   // one site per thread
     static constexpr int GX = Prec<P>::GX;
-    static constexpr int BX = TX + 2 * GX;            // box columns
+    static constexpr int BX = TX + 2 * GX;            // box columns (sites)
     static constexpr int BY = TY + 2 * kGY;           // box rows
-    static constexpr int SPEC = 9 * BX * BY;          // elements per species box
-    static constexpr int SPEC_BYTES = SPEC * (int)sizeof(T);
-    static constexpr int SPEC_STRIDE = (SPEC_BYTES + 127) / 128 * 128;
+    static constexpr int BOX_BYTES = 9 * BY * BX * (int)sizeof(T2);    // both species
+    static constexpr int BOX_STRIDE = (BOX_BYTES + 127) / 128 * 128;
     static constexpr int RX = TX + 4, RY = TY + 4;    // rho/Psi tile (2-cell halo)
-    static constexpr int RHOPSI = (4 * RX * RY * (int)sizeof(C) + 127) / 128 * 128;
-    static constexpr int STAGE_SPEC = 9 * TY * TX * (int)sizeof(T);  // output tile, one species
-    static constexpr int STAGE_OFF = 4 * SPEC_STRIDE + RHOPSI;
-    static constexpr int SMEM = STAGE_OFF + 2 * STAGE_SPEC + 128;     // step: 2 boxes + staging
-    static constexpr int SMEM_OBS = 2 * SPEC_STRIDE + RHOPSI + 128;   // observe: 1 box
-    static_assert(STAGE_SPEC % 128 == 0, "staging alignment");
-    static_assert((BX * sizeof(T)) % 16 == 0, "TMA box rows must be 16-byte multiples");
+    static constexpr int RHOPSI = (2 * RX * RY * (int)sizeof(C2) + 127) / 128 * 128;
+    static constexpr int STAGE_BYTES = 9 * TY * TX * (int)sizeof(T2);  // output tile
+    static constexpr int STAGE_OFF = 2 * BOX_STRIDE + RHOPSI;
+    static constexpr int SMEM = STAGE_OFF + STAGE_BYTES + 128;     // step: 2 boxes + staging
+    static constexpr int SMEM_OBS = BOX_STRIDE + RHOPSI + 128;     // observe: 1 box
+    static_assert(STAGE_BYTES % 128 == 0, "staging alignment");
+    static_assert((BX * sizeof(T2)) % 16 == 0, "TMA box rows must be 16-byte multiples");
+    static_assert(2 * BX <= 256 && 2 * TX <= 256 && BY <= 256, "TMA box extent");
     static_assert(GX >= 3 && (GX * sizeof(T)) % 16 == 0, "ghost width");
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };

@@ -40,3 +40,33 @@ def gpu_pops_as_oracle(f):
 
 def rel_err(a, b):
     return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def round_half(x):
+    """Round FP64 values to IEEE binary16, nearest-even (numpy's conversion)."""
+    return np.asarray(x, dtype=np.float64).astype(np.float16).astype(np.float64)
+
+
+def round_bf16(x):
+    """Round FP64 values to bfloat16 (7 fraction bits), nearest-even, directly
+    from the FP64 bits (values well inside the normal range)."""
+    b = np.ascontiguousarray(x, dtype=np.float64).view(np.uint64)
+    lsb = (b >> np.uint64(45)) & np.uint64(1)
+    b = (b + np.uint64((1 << 44) - 1) + lsb) & ~np.uint64((1 << 45) - 1)
+    return b.view(np.float64)
+
+
+def ulp16(x, fmt):
+    """Spacing of the 16-bit format at |x| (binary16: 10 fraction bits,
+    subnormal spacing 2^-24; bfloat16: 7 fraction bits)."""
+    ax = np.maximum(np.abs(np.asarray(x, dtype=np.float64)), 1e-300)
+    e = np.floor(np.log2(ax))
+    if fmt == "fp16":
+        return np.power(2.0, np.maximum(e, -14.0) - 10.0)
+    return np.power(2.0, e - 7.0)
+
+
+def offsets(f, rho_ref):
+    """Oracle-layout populations f (ny, nx, 2, 9) -> offsets f - w_i rho_ref."""
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    return f - w * rho_ref

@@ -196,3 +196,45 @@ def test_nonfinite_is_reported(lb):
         g.sync()
     assert e.value.status == lb.LB_ERR_NONFINITE
     g.close()
+
+
+# ----------------------------------------------------------- FP16 / BF16
+@pytest.mark.parametrize("fmt", ["fp16", "bf16"])
+@pytest.mark.parametrize("boundary", [0, 1])
+def test_half_offset_one_step(lb, O, fmt, boundary):
+    """One step from the same quantised state: the oracle advances the
+    quantised initial populations in FP64 and the result is compared, as
+    offsets h = f - w_i rho_ref, with the GPU's 16-bit output: at most one
+    unit in the last place of the format (FP32 arithmetic, one rounding)."""
+    from _pair import offsets, round_bf16, round_half, ulp16
+    rnd = round_half if fmt == "fp16" else round_bf16
+    m = model(72, 40, boundary=boundary, u_wall=0.02 if boundary else 0.0)
+    P = oracle_params(O, m)
+    rref = float(np.float32(m["rho0"]))       # offsets are taken from rho_ref in FP32
+    g = lb.Lattice(gpu_params(lb, m, fmt)).init_seeded(6)
+    f0 = O.init_seeded(P, 6)
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    h0 = rnd(offsets(f0, rref))
+    assert np.array_equal(offsets(gpu_pops_as_oracle(g.populations()), rref), h0)
+    f = h0 + w * rref
+    O.run(P, f, 1)
+    g.step(1)
+    want = offsets(f, rref)
+    got = offsets(gpu_pops_as_oracle(g.populations()), rref)
+    err = np.abs(got - want)
+    assert (err <= ulp16(want, fmt) * 1.0 + 1e-9).all(), err.max()
+    g.close()
+
+
+@pytest.mark.parametrize("fmt,tol", [("fp16", 5e-3), ("bf16", 4e-2)])
+def test_half_offset_20_steps(lb, O, fmt, tol):
+    """20 steps of the plain configuration: densities within the rounding
+    accumulated over the steps (relative to the FP64 oracle)."""
+    m = model(128, 128)
+    P, f, _, g = run_both(lb, O, m, 20, precision=fmt, seed=0)
+    ra, rb, _, _ = O.fields(P, f)
+    ga, gb, _, _ = g.fields()
+    err = max(rel_err(ga, ra), rel_err(gb, rb))
+    print(f"{fmt} 20-step relative error {err:.3e}")
+    assert err < tol
+    g.close()
