@@ -18,11 +18,12 @@ LIB = os.path.join(PKG, "liblbgb.so")
 # per storage precision so that the four compilations run in parallel.
 UNITS = [("lb_kernels.cu", [f"-DLB_PREC={p}"], f"lb_kernels_p{p}.o") for p in range(4)] + [
     ("lb_dispatch.cu", [], "lb_dispatch.o"),
+    ("lb_engine.cu", [], "lb_engine.o"),
     ("lb_api.cu", [], "lb_api.o"),
     ("lb_noalloc.cu", [], "lb_noalloc.o"),
 ]
 SOURCES = sorted({u[0] for u in UNITS})
-HEADERS = ["lb_internal.h", "lb_layout.cuh"]
+HEADERS = ["lb_internal.h", "lb_layout.cuh", "lb_engine.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

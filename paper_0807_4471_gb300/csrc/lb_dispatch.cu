@@ -18,10 +18,17 @@ int kernel_tile_x(int p) { LB_SWITCH(p, return Layout<P>::TX) return 0; }
 int kernel_tile_y(int p) { LB_SWITCH(p, return Layout<P>::TY) return 0; }
 int kernel_ghost_x(int p) { LB_SWITCH(p, return Layout<P>::GX) return 0; }
 int kernel_elem_bytes(int p) { LB_SWITCH(p, return (int)sizeof(typename Layout<P>::T)) return 0; }
+int kernel_smem_obs_bytes(int p) { LB_SWITCH(p, return Layout<P>::SMEM_OBS) return 0; }
+int kernel_block_rows(int p) { LB_SWITCH(p, return Layout<P>::TYB) return 0; }
 
-cudaError_t launch_step(int precision, const CUtensorMap* tin, const CUtensorMap* tout,
-                        const void* args, int obs, dim3 grid, cudaStream_t s) {
-    LB_SWITCH(precision, return launch_step_prec<P>(tin, tout, args, obs, grid, s))
+cudaError_t launch_step(int precision, const void* args, int variant, dim3 grid, cudaStream_t s) {
+    LB_SWITCH(precision, return launch_step_prec<P>(args, variant, grid, s))
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_observe(int precision, const CUtensorMap* tin, const void* args, dim3 grid,
+                           cudaStream_t s) {
+    LB_SWITCH(precision, return launch_observe_prec<P>(tin, args, grid, s))
     return cudaErrorInvalidValue;
 }
 

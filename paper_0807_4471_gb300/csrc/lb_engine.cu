@@ -1,0 +1,496 @@
+// lb_engine.cu -- host-side engine shared by the single-lattice ABI and the
+// lattice pool: parameter validation, device regions, TMA descriptors,
+// model coefficients, lattice descriptors, the work partition and launch of
+// the persistent step kernel, and the observe/initialise helpers.  Every
+// step of the model runs in the kernels of lb_kernels.cu.
+#include "lb_engine.h"
+
+#include <cmath>
+#include <cstring>
+
+namespace lbgb {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Multi-range weights p(|d|^2) (8th-order isotropic, second moment 1/3) and
+// the D2Q9 weights w(|d|^2), for the 12 pair representatives used by the
+// kernels: (1,0) (0,1) (1,1) (-1,1) (2,0) (0,2) (2,1) (1,2) (-1,2) (-2,1)
+// (2,2) (-2,2).
+static const int kRepC2[12] = {1, 1, 2, 2, 4, 4, 5, 5, 5, 5, 8, 8};
+static double p_weight(int c2) {
+    switch (c2) {
+        case 1: return 4.0 / 63.0;
+        case 2: return 4.0 / 135.0;
+        case 4: return 1.0 / 180.0;
+        case 5: return 2.0 / 945.0;
+        case 8: return 1.0 / 15120.0;
+    }
+    return 0.0;
+}
+static double w_weight(int c2) { return c2 == 1 ? 1.0 / 9.0 : c2 == 2 ? 1.0 / 36.0 : 0.0; }
+
+lb_status validate_params(const lb_params* p) {
+    if (!p) return LB_ERR_INVALID;
+    if (p->nx < 8 || p->ny < 8 || p->nx > (1 << 20) || p->ny > (1 << 19)) return LB_ERR_INVALID;
+    if (p->boundary != LB_PERIODIC && p->boundary != LB_COUETTE) return LB_ERR_INVALID;
+    if (p->precision < LB_FP64 || p->precision > LB_BF16_OFFSET) return LB_ERR_INVALID;
+    if (p->psi_form != LB_PSI_SQRT_RHO0 && p->psi_form != LB_PSI_RHO0) return LB_ERR_INVALID;
+    if (p->force_scheme != LB_FORCE_SHIFT && p->force_scheme != LB_FORCE_SOURCE) return LB_ERR_INVALID;
+    if (!(p->tau_A > 0.5) || !(p->tau_B > 0.5) || !(p->rho0 > 0.0)) return LB_ERR_INVALID;
+    if (p->stress_every < 1 || p->stress_t0 < 0) return LB_ERR_INVALID;
+    const double vals[] = {p->tau_A, p->tau_B, p->G_A1, p->G_A2, p->G_B1, p->G_B2, p->G_X,
+                           p->rho0, p->u_wall, p->init_amp, p->rho_ref, p->g_x, p->kolmo_amp,
+                           p->kolmo_k};
+    for (double v : vals)
+        if (!std::isfinite(v)) return LB_ERR_INVALID;
+    if (p->init_amp < 0.0 || p->init_amp >= 1.0 || p->rho_ref < 0.0) return LB_ERR_INVALID;
+    return LB_OK;
+}
+
+lb_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return LB_OK;
+    cudaGetLastError();
+    if (e == cudaErrorMemoryAllocation) return LB_ERR_NOMEM;
+    return LB_ERR_CUDA;
+}
+
+int device_sms(int device) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms < 1)
+        sms = 1;
+    return sms;
+}
+
+static Geom make_geom(const lb_params* p) {
+    Geom g;
+    const int prec = p->precision;
+    const int es = kernel_elem_bytes(prec);
+    const int gx = kernel_ghost_x(prec);
+    // a row of pairs is 2 * pitch * es bytes: keep pitch * es a multiple of 16
+    const int align_pairs = 16 / es;
+    const int box_w = kernel_tile_x(prec) + 2 * gx;
+    int pitch = (int)align_up((size_t)(p->nx + 2 * gx), (size_t)align_pairs);
+    if (pitch < box_w) pitch = box_w;
+    g.nx = p->nx;
+    g.ny = p->ny;
+    g.pitch = pitch;
+    g.rows = p->ny + 2 * kGY;
+    g.plane = (long long)g.rows * g.pitch;
+    g.gx = gx;
+    g.periodic = p->boundary == LB_PERIODIC ? 1 : 0;
+    return g;
+}
+
+// Device region of one lattice: stats, observe slots, two buffers.
+struct Region {
+    size_t stats, slots, f0, f1, total, fbytes;
+};
+static Region region_layout(const lb_params* p) {
+    Geom g = make_geom(p);
+    const int tx = kernel_tile_x(p->precision), ty = kernel_tile_y(p->precision);
+    const size_t ntiles = (size_t)((p->nx + tx - 1) / tx) * (size_t)((p->ny + ty - 1) / ty);
+    Region r;
+    size_t off = 0;
+    r.stats = off;
+    off = align_up(off + sizeof(DevStats), kAlign);
+    r.slots = off;
+    off = align_up(off + sizeof(double) * 4 * ntiles, kAlign);
+    r.fbytes = align_up((size_t)18 * (size_t)g.plane * (size_t)kernel_elem_bytes(p->precision), kAlign);
+    r.f0 = off;
+    off += r.fbytes;
+    r.f1 = off;
+    off += r.fbytes;
+    r.total = off;
+    return r;
+}
+
+size_t lattice_bytes(const lb_params* p) { return region_layout(p).total; }
+
+template <typename C>
+static void fill_coef(Coef<C>& k, const lb_params* p) {
+    const double Ga[2] = {p->G_A1, p->G_B1};
+    const double Gr[2] = {p->G_A2, p->G_B2};
+    for (int s = 0; s < 2; ++s)
+        for (int r = 0; r < 12; ++r) {
+            const int c2 = kRepC2[r];
+            const double v = (r < 4 ? Ga[s] * w_weight(c2) : 0.0) + Gr[s] * p_weight(c2);
+            k.K[s][r] = (C)v;
+        }
+    for (int r = 0; r < 4; ++r) k.W[r] = (C)w_weight(kRepC2[r]);
+    // Offsets are taken from rho_ref rounded to the compute precision, so that
+    // rho = rho_ref + sum_i h_i holds with the same rho_ref on every path.
+    const double rref = (double)(C)(p->rho_ref > 0.0 ? p->rho_ref : p->rho0);
+    const double pref = p->psi_form == LB_PSI_RHO0 ? p->rho0 : std::sqrt(p->rho0);
+    k.gx_rho0 = (C)(p->G_X / p->rho0);
+    k.rho_ref = (C)rref;
+    k.psi_ref = (C)(pref * (1.0 - std::exp(-rref / p->rho0)));
+    k.psi_scale = (C)(pref * std::exp(-rref / p->rho0));
+    k.inv_rho0 = (C)(1.0 / p->rho0);
+    k.tau[0] = (C)p->tau_A;
+    k.tau[1] = (C)p->tau_B;
+    k.omega[0] = (C)(1.0 / p->tau_A);
+    k.omega[1] = (C)(1.0 / p->tau_B);
+    k.u_wall = (C)p->u_wall;
+    k.g_x = (C)p->g_x;
+    k.kolmo_amp = (C)p->kolmo_amp;
+    k.kolmo_w = (C)(2.0 * M_PI * p->kolmo_k / p->ny);
+    k.source = p->force_scheme == LB_FORCE_SOURCE ? 1 : 0;
+    k.has_accel = (p->g_x != 0.0 || p->kolmo_amp != 0.0) ? 1 : 0;
+}
+
+template <typename C>
+static LatVals<C> vals_of(const Coef<C>& k) {
+    LatVals<C> v;
+    v.rho_ref = k.rho_ref;
+    v.psi_ref = k.psi_ref;
+    v.psi_scale = k.psi_scale;
+    v.inv_rho0 = k.inv_rho0;
+    v.gx_rho0 = k.gx_rho0;
+    v.u_wall = k.u_wall;
+    return v;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    }
+    return fn;
+}
+
+// TMA descriptor of one population buffer: 9 direction planes of interleaved
+// (A, B) pairs, a row holding 2 * pitch elements.  Box: cols pairs x rows x
+// 9 planes.
+static lb_status make_tmap(CUtensorMap* m, int precision, const Geom& g, void* base, int cols,
+                           int rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return LB_ERR_CUDA;
+    const int es = kernel_elem_bytes(precision);
+    CUtensorMapDataType dt = precision == LB_FP64   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                             : precision == LB_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                    : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    cuuint64_t dims[3] = {(cuuint64_t)(2 * g.pitch), (cuuint64_t)g.rows, 9};
+    cuuint64_t strides[2] = {(cuuint64_t)(2 * g.pitch) * es,
+                             (cuuint64_t)g.rows * (cuuint64_t)(2 * g.pitch) * es};
+    cuuint32_t box[3] = {(cuuint32_t)(2 * cols), (cuuint32_t)rows, 9};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(m, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? LB_OK : LB_ERR_CUDA;
+}
+
+lb_status lattice_setup(Lattice& L, const lb_params* p, char* region) {
+    L.p = *p;
+    L.g = make_geom(p);
+    Region r = region_layout(p);
+    L.region = region;
+    L.st = reinterpret_cast<DevStats*>(region + r.stats);
+    L.slots = reinterpret_cast<double*>(region + r.slots);
+    L.fbuf[0] = region + r.f0;
+    L.fbuf[1] = region + r.f1;
+    L.fbytes = r.fbytes;
+    L.cur = 0;
+    L.pull = 0;
+    L.inited = false;
+    L.t = 0;
+    L.err_latched = 0;
+    const int tx = kernel_tile_x(p->precision), ty = kernel_tile_y(p->precision);
+    L.nstrips = (p->nx + tx - 1) / tx;
+    L.ntiles_y = (p->ny + ty - 1) / ty;
+    L.seg = 1;
+    fill_coef(L.kd, p);
+    fill_coef(L.kf, p);
+    const int bx = tx + 2 * L.g.gx;
+    lb_status s = LB_OK;
+    for (int b = 0; b < 2 && s == LB_OK; ++b) {
+        s = make_tmap(&L.tblock[b], p->precision, L.g, L.fbuf[b], bx, kernel_block_rows(p->precision));
+        if (s == LB_OK) s = make_tmap(&L.ttile[b], p->precision, L.g, L.fbuf[b], tx, ty);
+        if (s == LB_OK) s = make_tmap(&L.tobs[b], p->precision, L.g, L.fbuf[b], bx, ty + 2 * kGY);
+    }
+    return s;
+}
+
+// Load-balance model of the persistent step kernel: items are segments of
+// `seg` tiles of the column strips; CTA b takes items b, b + G, ...  A CTA's
+// cost is its tiles plus a quarter tile per item (the first tile of an item
+// computes 12 rather than 8 deviation rows).  Returns the seg in [1, 64]
+// minimising the most loaded CTA (ties: longer segments).
+int choose_seg(const int* nstrips, const int* ntiles_y, int nlat, int G) {
+    int best_seg = 1;
+    double best = 1e300;
+    std::vector<double> cost;
+    for (int seg = 1; seg <= 64; ++seg) {
+        long long items = 0;
+        for (int l = 0; l < nlat; ++l) items += (long long)nstrips[l] * ((ntiles_y[l] + seg - 1) / seg);
+        const int g = items < G ? (int)items : G;
+        if (g <= 0) continue;
+        cost.assign((size_t)g, 0.0);
+        long long it = 0;
+        for (int l = 0; l < nlat; ++l) {
+            const int nseg = (ntiles_y[l] + seg - 1) / seg;
+            for (int sg = 0; sg < nseg; ++sg) {
+                const int size = (sg + 1) * seg <= ntiles_y[l] ? seg : ntiles_y[l] - sg * seg;
+                for (int sx = 0; sx < nstrips[l]; ++sx, ++it) cost[(size_t)(it % g)] += size + 0.25;
+            }
+        }
+        double mx = 0.0;
+        for (double c : cost) mx = c > mx ? c : mx;
+        if (mx <= best) {
+            best = mx;
+            best_seg = seg;
+        }
+    }
+    return best_seg;
+}
+
+template <typename C>
+static void fill_desc(LatDesc<C>& d, const Lattice& L, const Coef<C>& k, int item0) {
+    memset(&d, 0, sizeof(d));
+    for (int b = 0; b < 2; ++b) {
+        d.tin[b] = L.tblock[b];
+        d.tout[b] = L.ttile[b];
+        d.fbuf[b] = L.fbuf[b];
+    }
+    d.g = L.g;
+    d.v = vals_of(k);
+    d.st = L.st;
+    d.item0 = item0;
+    d.nstrips = L.nstrips;
+    d.ntiles_y = L.ntiles_y;
+    d.seg = L.seg;
+    d.stress_every = L.p.stress_every;
+    d.stress_t0 = L.p.stress_t0;
+}
+
+lb_status launch_build(Launch& Ln, Lattice* const* lats, int nlat, void* descs, double* slots,
+                       unsigned int* ticket, int sms, cudaStream_t stream, void* host_scratch) {
+    if (nlat < 1) return LB_ERR_INVALID;
+    const int prec = lats[0]->p.precision;
+    std::vector<int> ns((size_t)nlat), nt((size_t)nlat);
+    bool allper = true, gen = false;
+    for (int l = 0; l < nlat; ++l) {
+        ns[(size_t)l] = lats[l]->nstrips;
+        nt[(size_t)l] = lats[l]->ntiles_y;
+        allper = allper && lats[l]->g.periodic;
+        gen = gen || lats[l]->kd.source || lats[l]->kd.has_accel;
+    }
+    const int seg = choose_seg(ns.data(), nt.data(), nlat, sms);
+    int items = 0;
+    const size_t dsz = prec == LB_FP64 ? sizeof(LatDesc<double>) : sizeof(LatDesc<float>);
+    char* hs = reinterpret_cast<char*>(host_scratch);
+    for (int l = 0; l < nlat; ++l) {
+        lats[l]->seg = seg;
+        if (prec == LB_FP64)
+            fill_desc(*reinterpret_cast<LatDesc<double>*>(hs + l * dsz), *lats[l], lats[l]->kd, items);
+        else
+            fill_desc(*reinterpret_cast<LatDesc<float>*>(hs + l * dsz), *lats[l], lats[l]->kf, items);
+        items += lats[l]->nstrips * ((lats[l]->ntiles_y + seg - 1) / seg);
+    }
+    cudaError_t e = cudaMemcpyAsync(descs, hs, dsz * nlat, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);   // host_scratch is reused
+    if (e != cudaSuccess) return cuda_status(e);
+    Ln.precision = prec;
+    Ln.variant = (allper ? 1 : 0) | (gen ? 2 : 0);
+    Ln.grid = dim3((unsigned)(items < sms ? items : sms), 1, 1);
+    Ln.nitems = items;
+    Ln.seg = seg;
+    if (prec == LB_FP64) {
+        BatchArgs<double>& a = Ln.ad;
+        a.k = lats[0]->kd;
+        a.lat = reinterpret_cast<const LatDesc<double>*>(descs);
+        a.nlat = nlat;
+        a.nitems = items;
+        a.slots = slots;
+        a.ticket = ticket;
+    } else {
+        BatchArgs<float>& a = Ln.af;
+        a.k = lats[0]->kf;
+        a.lat = reinterpret_cast<const LatDesc<float>*>(descs);
+        a.nlat = nlat;
+        a.nitems = items;
+        a.slots = slots;
+        a.ticket = ticket;
+    }
+    return LB_OK;
+}
+
+lb_status launch_run(const Launch& Ln, cudaStream_t s) {
+    const void* args = Ln.precision == LB_FP64 ? (const void*)&Ln.ad : (const void*)&Ln.af;
+    return cuda_status(launch_step(Ln.precision, args, Ln.variant, Ln.grid, s));
+}
+
+lb_status lattice_observe(Lattice& L, int obs, double* out, int q0, int q1, cudaStream_t s) {
+    const int tx = kernel_tile_x(L.p.precision), ty = kernel_tile_y(L.p.precision);
+    dim3 grid((unsigned)((L.p.nx + tx - 1) / tx), (unsigned)((L.p.ny + ty - 1) / ty), 1);
+    cudaError_t e;
+    if (L.p.precision == LB_FP64) {
+        StepArgs<double> a;
+        memset(&a, 0, sizeof(a));
+        a.g = L.g;
+        a.k = L.kd;
+        a.st = L.st;
+        a.slots = L.slots;
+        a.pull = L.pull;
+        a.obs = obs;
+        a.obs_out = out;
+        a.q0 = q0;
+        a.q1 = q1;
+        e = launch_observe(L.p.precision, &L.tobs[L.cur], &a, grid, s);
+    } else {
+        StepArgs<float> a;
+        memset(&a, 0, sizeof(a));
+        a.g = L.g;
+        a.k = L.kf;
+        a.st = L.st;
+        a.slots = L.slots;
+        a.pull = L.pull;
+        a.obs = obs;
+        a.obs_out = out;
+        a.q0 = q0;
+        a.q1 = q1;
+        e = launch_observe(L.p.precision, &L.tobs[L.cur], &a, grid, s);
+    }
+    return cuda_status(e);
+}
+
+lb_status lattice_read_stats(Lattice& L, DevStats* out, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(out, L.st, sizeof(DevStats), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    L.err_latched |= out->err;
+    if (L.err_latched & ERR_TIMEOUT) return LB_ERR_TIMEOUT;
+    if (L.err_latched & ERR_NONFINITE) return LB_ERR_NONFINITE;
+    return LB_OK;
+}
+
+static lb_status lattice_reset(Lattice& L, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(L.st, 0, sizeof(DevStats), s);   // t = 0, cur = 0, pull = 0
+    if (e != cudaSuccess) return cuda_status(e);
+    L.t = 0;
+    L.cur = 0;
+    L.pull = 0;
+    L.inited = true;
+    L.err_latched = 0;
+    return LB_OK;
+}
+
+static void* coef_ptr(Lattice& L) {
+    return L.p.precision == LB_FP64 ? (void*)&L.kd : (void*)&L.kf;
+}
+
+lb_status lattice_init_seeded(Lattice& L, uint64_t seed, cudaStream_t s) {
+    lb_status st = lattice_reset(L, s);
+    if (st != LB_OK) return st;
+    return cuda_status(launch_init_seeded(L.p.precision, L.g, coef_ptr(L), L.fbuf[0], L.p.rho0,
+                                          L.p.init_amp, L.p.u_wall, L.p.init_shear,
+                                          (unsigned long long)seed, s));
+}
+
+lb_status lattice_init_fields(Lattice& L, const double* rho_A, const double* rho_B,
+                              const double* ux, const double* uy, cudaStream_t s) {
+    lb_status st = lattice_reset(L, s);
+    if (st != LB_OK) return st;
+    const size_t n = (size_t)L.p.nx * L.p.ny;
+    // Stage the four FP64 fields in buffer 1 (its size, 18 planes of at least
+    // 2 bytes per padded site, always exceeds 32 bytes per site).
+    double* stage = reinterpret_cast<double*>(L.fbuf[1]);
+    cudaError_t e = cudaMemcpyAsync(stage, rho_A, n * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(stage + n, rho_B, n * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = ux ? cudaMemcpyAsync(stage + 2 * n, ux, n * 8, cudaMemcpyHostToDevice, s)
+               : cudaMemsetAsync(stage + 2 * n, 0, n * 8, s);
+    if (e == cudaSuccess)
+        e = uy ? cudaMemcpyAsync(stage + 3 * n, uy, n * 8, cudaMemcpyHostToDevice, s)
+               : cudaMemsetAsync(stage + 3 * n, 0, n * 8, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    e = launch_init_fields(L.p.precision, L.g, coef_ptr(L), L.fbuf[0], stage, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return cuda_status(e);
+}
+
+void lattice_advanced(Lattice& L, long long n) {
+    if (n <= 0) return;
+    L.t += n;
+    L.cur ^= (int)(n & 1);
+    L.pull = 1;
+}
+
+lb_status lattice_fields(Lattice& L, double* rho_A, double* rho_B, double* ux, double* uy,
+                         cudaStream_t s) {
+    const size_t n = (size_t)L.p.nx * L.p.ny;
+    double* out = reinterpret_cast<double*>(L.fbuf[1 - L.cur]);
+    lb_status st = lattice_observe(L, OBS_FIELDS, out, 0, 0, s);
+    if (st != LB_OK) return st;
+    double* dst[4] = {rho_A, rho_B, ux, uy};
+    for (int k = 0; k < 4; ++k)
+        if (dst[k]) {
+            cudaError_t e = cudaMemcpyAsync(dst[k], out + k * n, n * 8, cudaMemcpyDeviceToHost, s);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+    DevStats ds;
+    return lattice_read_stats(L, &ds, s);
+}
+
+lb_status lattice_populations(Lattice& L, double* f, cudaStream_t s) {
+    const size_t n = (size_t)L.p.nx * L.p.ny;
+    double* out = reinterpret_cast<double*>(L.fbuf[1 - L.cur]);
+    int per = (int)(L.fbytes / (n * 8));
+    if (per < 1) return LB_ERR_UNSUPPORTED;
+    if (per > 18) per = 18;
+    for (int q0 = 0; q0 < 18; q0 += per) {
+        const int q1 = q0 + per < 18 ? q0 + per : 18;
+        lb_status st = lattice_observe(L, OBS_POPS, out, q0, q1, s);
+        if (st != LB_OK) return st;
+        cudaError_t e = cudaMemcpyAsync(f + (size_t)q0 * n, out, (size_t)(q1 - q0) * n * 8,
+                                        cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    DevStats ds;
+    return lattice_read_stats(L, &ds, s);
+}
+
+lb_status lattice_stress(Lattice& L, lb_stress_out* out, cudaStream_t s) {
+    lb_status st = lattice_observe(L, OBS_TOTALS, nullptr, 0, 0, s);
+    if (st != LB_OK) return st;
+    DevStats ds;
+    st = lattice_read_stats(L, &ds, s);
+    memset(out, 0, sizeof(*out));
+    out->mass_A = ds.totals[0];
+    out->mass_B = ds.totals[1];
+    out->mom_x = ds.totals[2];
+    out->mom_y = ds.totals[3];
+    out->samples = ds.samples;
+    out->step = L.t;
+    if (ds.samples > 0) {
+        out->sigma_bot = ds.sum_bot / (double)ds.samples;
+        out->sigma_top = ds.sum_top / (double)ds.samples;
+        out->sigma_mean = 0.5 * (out->sigma_bot - out->sigma_top);
+    }
+    const double rate = 2.0 * L.p.u_wall / L.p.ny;
+    const double mass = ds.totals[0] + ds.totals[1];
+    const double rho_mean = mass / ((double)L.p.nx * L.p.ny);
+    if (L.p.boundary == LB_COUETTE && rate != 0.0 && rho_mean > 0.0 && ds.samples > 0) {
+        out->nu_eff = out->sigma_mean / (rate * rho_mean);
+        const double tau = mass > 0.0 ? (L.p.tau_A * ds.totals[0] + L.p.tau_B * ds.totals[1]) / mass
+                                      : L.p.tau_A;
+        const double nu0 = (tau - 0.5) / 3.0;
+        out->response_R = out->nu_eff != 0.0 ? nu0 / out->nu_eff : 0.0;
+    }
+    return st;
+}
+
+}  // namespace lbgb

@@ -15,13 +15,15 @@ namespace lbgb {
 // Device-resident counters and accumulators of one lattice.
 struct DevStats {
     unsigned int err;       // bit 0: non-finite density, bit 1: TMA wait timeout
-    unsigned int ticket;    // CTA arrival counter of the last-block reductions
+    unsigned int ticket;    // CTA arrival counter of the observe reductions
     long long t;            // completed time steps
     double sum_bot;         // sum of per-step bottom-wall samples
     double sum_top;         // sum of per-step top-wall samples
     long long samples;      // number of samples in the sums
     double totals[4];       // last observe pass: mass_A, mass_B, mom_x, mom_y
-    double pad_[7];
+    int cur;                // buffer holding the current state (0 or 1)
+    int pull;               // 1: it holds post-collision f*(t-1); 0: f(t) in place
+    double pad_[6];
 };
 static_assert(sizeof(DevStats) == 128, "DevStats is one 128-byte line");
 
@@ -63,6 +65,42 @@ struct Coef {
     int has_accel;     // 1 if g_x or kolmo_amp is nonzero
 };
 
+// Values that vary between the lattices of one step launch.
+template <typename C>
+struct LatVals {
+    C rho_ref, psi_ref, psi_scale, inv_rho0, gx_rho0, u_wall;
+};
+
+// One lattice of a step launch, in device memory (128-byte aligned for the
+// tensor maps).  Both buffers are described; the device-side DevStats::cur
+// says which one holds the current state.
+template <typename C>
+struct alignas(128) LatDesc {
+    CUtensorMap tin[2];    // 8-row block loads of buffer b: box {2 BX, 8, 9}
+    CUtensorMap tout[2];   // full-tile stores into buffer b: box {2 TX, TY, 9}
+    Geom g;
+    LatVals<C> v;
+    void* fbuf[2];
+    DevStats* st;
+    int item0;             // first work item of this lattice in the launch
+    int nstrips;           // ceil(nx / TX)
+    int ntiles_y;          // ceil(ny / TY)
+    int seg;               // tiles per work item (a segment of a column strip)
+    int stress_every;
+    long long stress_t0;
+};
+
+// Arguments of the (multi-lattice) step kernel.
+template <typename C>
+struct BatchArgs {
+    Coef<C> k;                  // coefficients shared by all lattices of the launch
+    const LatDesc<C>* lat;      // nlat descriptors, ordered by item0
+    int nlat;
+    int nitems;                 // total work items
+    double* slots;              // [nitems][2] wall-momentum partial sums
+    unsigned int* ticket;       // CTA arrival counter of the launch (zero between launches)
+};
+
 // Observe-mode outputs (the kernel writes FP64 planes of nx*ny values).
 enum ObsKind : int { OBS_NONE = 0, OBS_FIELDS = 1, OBS_POPS = 2, OBS_TOTALS = 3 };
 
@@ -87,13 +125,17 @@ int kernel_tile_x(int precision);
 int kernel_tile_y(int precision);
 int kernel_ghost_x(int precision);
 int kernel_elem_bytes(int precision);
+int kernel_smem_obs_bytes(int precision);
+int kernel_block_rows(int precision);
 
 // obs = OBS_NONE: the persistent step kernel over `grid` CTAs; otherwise the
 // observe kernel with one CTA per tile.
-// tin: load descriptor of the input buffer; tout: store descriptor of the
-// output buffer (unused by the observe kernel).
-cudaError_t launch_step(int precision, const CUtensorMap* tin, const CUtensorMap* tout,
-                        const void* args, int obs, dim3 grid, cudaStream_t s);
+// Step: the persistent multi-lattice kernel (args: BatchArgs<C>), variant
+// bit 0 = every lattice periodic, bit 1 = general forcing.  Observe: one
+// lattice, one CTA per tile (args: StepArgs<C>, tin: tile-box load map).
+cudaError_t launch_step(int precision, const void* args, int variant, dim3 grid, cudaStream_t s);
+cudaError_t launch_observe(int precision, const CUtensorMap* tin, const void* args, dim3 grid,
+                           cudaStream_t s);
 cudaError_t launch_init_seeded(int precision, const Geom& g, const void* coef, void* fout,
                                double rho0, double amp, double u_wall, int init_shear,
                                unsigned long long seed, cudaStream_t s);
@@ -103,8 +145,10 @@ cudaError_t launch_init_fields(int precision, const Geom& g, const void* coef, v
 // Per-precision launchers, one explicit instantiation per compilation of
 // lb_kernels.cu (-DLB_PREC=P).
 template <int P>
-cudaError_t launch_step_prec(const CUtensorMap* tin, const CUtensorMap* tout, const void* args,
-                             int obs, dim3 grid, cudaStream_t s);
+cudaError_t launch_step_prec(const void* args, int variant, dim3 grid, cudaStream_t s);
+template <int P>
+cudaError_t launch_observe_prec(const CUtensorMap* tin, const void* args, dim3 grid,
+                                cudaStream_t s);
 template <int P>
 cudaError_t launch_init_prec(const Geom& g, const void* coef, void* fout, int mode,
                              const double* fields, double rho0, double amp, double u_wall,

@@ -130,36 +130,40 @@ __device__ __forceinline__ C sum9(const C h[9]) {
     return ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
 }
 
-// The offsets h_i(r, t) of both species at lattice site (x, y), whose box
-// coordinates are (sx, sy).  pull = 1: streamed from h*(r - c_i, t - 1), with
+// The offsets h_i(r, t) of both species at lattice row y.  bm, b0, bp point
+// at the site's pair in the staged rows y-1, y, y+1 of plane 0 (plane i is
+// PS pairs further).  pull = 1: streamed from h*(r - c_i, t - 1), with
 // halfway bounce-back at the Couette walls: f_i = f*_opp(i)(r)
 // + 6 w_i rho_w (c_i . u_w), rho_w the pre-streaming density of the
-// boundary node, rho_ref + sum_j h*_j(r).
-template <int P, bool PER>
-__device__ __forceinline__ void load_site(const typename Prec<P>::T2* box, int sx, int sy, int y,
-                                          const StepArgs<typename Prec<P>::C>& a,
+// boundary node, rho_ref + sum_j h*_j(r).  pull = 0: the state in place.
+template <int P, int PS>
+__device__ __forceinline__ void load_site(const typename Prec<P>::T2* bm,
+                                          const typename Prec<P>::T2* b0,
+                                          const typename Prec<P>::T2* bp, int y, bool per,
+                                          int pull, const Geom& g,
+                                          const LatVals<typename Prec<P>::C>& v,
                                           typename Prec<P>::C hA[9], typename Prec<P>::C hB[9]) {
-    typedef Layout<P> L;
     typedef typename Prec<P>::C C;
     typedef typename Prec<P>::C2 C2;
-    if (a.pull) {
+    if (pull) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const C2 v = dec2(box[(i * L::BY + sy - cy(i)) * L::BX + sx - cx(i)]);
-            hA[i] = v.x;
-            hB[i] = v.y;
+            const typename Prec<P>::T2* r = cy(i) == 1 ? bm : (cy(i) == -1 ? bp : b0);
+            const C2 q = dec2(r[i * PS - cx(i)]);
+            hA[i] = q.x;
+            hB[i] = q.y;
         }
-        if (!PER && (y == 0 || y == a.g.ny - 1)) {
+        if (!per && (y == 0 || y == g.ny - 1)) {
             C sA[9], sB[9];
 #pragma unroll
             for (int j = 0; j < 9; ++j) {
-                const C2 v = dec2(box[(j * L::BY + sy) * L::BX + sx]);
-                sA[j] = v.x;
-                sB[j] = v.y;
+                const C2 q = dec2(b0[j * PS]);
+                sA[j] = q.x;
+                sB[j] = q.y;
             }
-            const C rwA = a.k.rho_ref + sum9(sA), rwB = a.k.rho_ref + sum9(sB);
+            const C rwA = v.rho_ref + sum9(sA), rwB = v.rho_ref + sum9(sB);
             const int up = (y == 0);                 // links arriving upward
-            const C uw = up ? -a.k.u_wall : a.k.u_wall;
+            const C uw = up ? -v.u_wall : v.u_wall;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 if ((up && cy(i) == 1) || (!up && cy(i) == -1)) {
@@ -172,9 +176,9 @@ __device__ __forceinline__ void load_site(const typename Prec<P>::T2* box, int s
     } else {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const C2 v = dec2(box[(i * L::BY + sy) * L::BX + sx]);
-            hA[i] = v.x;
-            hB[i] = v.y;
+            const C2 q = dec2(b0[i * PS]);
+            hA[i] = q.x;
+            hB[i] = q.y;
         }
     }
 }
@@ -182,8 +186,25 @@ __device__ __forceinline__ void load_site(const typename Prec<P>::T2* box, int s
 // Deviation of the pseudo-potential from Psi(rho_ref):
 // Psi(rho_ref + d) - Psi(rho_ref) = -P exp(-rho_ref/rho0) expm1(-d/rho0).
 template <typename C>
-__device__ __forceinline__ C dpsi_of(C d, const Coef<C>& k) {
-    return -k.psi_scale * cexpm1(-d * k.inv_rho0);
+__device__ __forceinline__ C dpsi_of(C d, const LatVals<C>& v) {
+    return -v.psi_scale * cexpm1(-d * v.inv_rho0);
+}
+
+// Density and pseudo-potential deviations (rho - rho_ref, Psi - Psi(rho_ref))
+// of both species at one site.
+template <int P, int PS>
+__device__ __forceinline__ void cell_dev(const typename Prec<P>::T2* bm,
+                                         const typename Prec<P>::T2* b0,
+                                         const typename Prec<P>::T2* bp, int y, bool per, int pull,
+                                         const Geom& g, const LatVals<typename Prec<P>::C>& v,
+                                         typename Prec<P>::C2& r, typename Prec<P>::C2& q) {
+    typedef typename Prec<P>::C C;
+    C hA[9], hB[9];
+    load_site<P, PS>(bm, b0, bp, y, per, pull, g, v, hA, hB);
+    r.x = sum9(hA);
+    r.y = sum9(hB);
+    q.x = dpsi_of(r.x, v);
+    q.y = dpsi_of(r.y, v);
 }
 
 // Post-collision offsets of one species (Eq. (1), BGK toward the
@@ -216,75 +237,38 @@ __device__ __forceinline__ void collide(const C h[9], C out[9], C drho, C rho, C
     }
 }
 
-// ------------------------------------------------------------- tile body
-// Phases 2-3 for one TX x TY tile whose f* box is in shared memory.
-// OBS = false: collision and write-back of f*(t) (+ wall momentum into red).
-// OBS = true : fields / populations / totals of the current state (red =
-//              mass_A, mass_B, mom_x, mom_y).
-// V: bit 0 = periodic in y (else Couette walls); bit 1 = general forcing
-// (additive source term or body acceleration checked at run time).
-template <int P, bool OBS, int V>
-__device__ __forceinline__ void tile_body(const typename Prec<P>::T2* __restrict__ box,
-                                          typename Prec<P>::C2* __restrict__ srho,
-                                          typename Prec<P>::C2* __restrict__ spsi, int x0, int y0,
-                                          const StepArgs<typename Prec<P>::C>& a, double red[4],
-                                          bool& bad, typename Prec<P>::T2* __restrict__ stage) {
-    typedef Layout<P> L;
-    typedef typename L::T2 T2;
-    typedef typename L::C C;
-    typedef typename L::C2 C2;
-    constexpr bool PER = (V & 1) != 0;
-    constexpr bool GEN = (V & 2) != 0;
-    const int tid = threadIdx.x;
-    const Geom& g = a.g;
+// Where a site update sends its result.
+template <typename T2>
+struct SiteOut {
+    T2* stage;             // staging tile slot of the site (full tiles), or null
+    T2* fout;              // output buffer (ragged tiles and ghost copies)
+    int obs;               // ObsKind (observe kernel) or OBS_NONE
+    double* obs_out;
+    int q0, q1;
+};
 
-    // 2. density and pseudo-potential deviations d_rho = rho - rho_ref,
-    // d_Psi = Psi(rho) - Psi(rho_ref), on the tile + 2-cell halo.
-    for (int c = tid; c < L::RX * L::RY; c += L::NT) {
-        const int ly = c / L::RX, lx = c - ly * L::RX;
-        const int y = y0 - 2 + ly;
-        if (!PER && (y < 0 || y >= g.ny)) continue;
-        C hA[9], hB[9];
-        load_site<P, PER>(box, lx - 2 + L::GX, ly - 2 + kGY, y, a, hA, hB);
-        const C rA = sum9(hA), rB = sum9(hB);
-        C2 r, q;
-        r.x = rA;
-        r.y = rB;
-        q.x = dpsi_of(rA, a.k);
-        q.y = dpsi_of(rB, a.k);
-        srho[ly * L::RX + lx] = r;
-        spsi[ly * L::RX + lx] = q;
-    }
-    if (!PER) {   // mirror the deviations about the halfway walls
-        __syncthreads();
-        for (int c = tid; c < L::RX * L::RY; c += L::NT) {
-            const int ly = c / L::RX, lx = c - ly * L::RX;
-            const int y = y0 - 2 + ly;
-            int ym;
-            if (y < 0) ym = -1 - y;
-            else if (y >= g.ny) ym = 2 * g.ny - 1 - y;
-            else continue;
-            const int lm = ym - (y0 - 2);
-            if (lm < 0 || lm >= L::RY) continue;
-            srho[ly * L::RX + lx] = srho[lm * L::RX + lx];
-            spsi[ly * L::RX + lx] = spsi[lm * L::RX + lx];
-        }
-    }
-    // the previous tile's bulk store must have read the staging tile
-    if (stage != nullptr && tid == 0) bulk_wait_read();
-    __syncthreads();
-
-    // 3. one site per thread: moments, forces, collision, write-back.
-    const int lx = tid % L::TX, ly = tid / L::TX;
-    const int x = x0 + lx, y = y0 + ly;
-    if (x >= g.nx || y >= g.ny) return;
+// One lattice site: moments, the force of Eq. (2) from the staged deviation
+// rows, and either the forced BGK collision and write-back (OBS = false) or
+// the observables (OBS = true).  ps[k] / rr[k]: Psi / rho deviation rows
+// y + k - 2, pointing at the site's column.  red accumulates the bottom/top
+// wall momentum (step) or mass_A, mass_B, mom_x, mom_y (observe).
+template <int P, bool OBS, bool GEN, int PS>
+__device__ __forceinline__ void site_update(
+    const typename Prec<P>::T2* bm, const typename Prec<P>::T2* b0,
+    const typename Prec<P>::T2* bp, const typename Prec<P>::C2* const ps[5],
+    const typename Prec<P>::C2* const rr[5], int x, int y, bool per, int pull, const Geom& g,
+    const LatVals<typename Prec<P>::C>& v, const Coef<typename Prec<P>::C>& k,
+    const SiteOut<typename Prec<P>::T2>& o, double red[4], bool& bad) {
+    typedef typename Prec<P>::T2 T2;
+    typedef typename Prec<P>::C C;
+    typedef typename Prec<P>::C2 C2;
     C h[2][9];
-    load_site<P, PER>(box, lx + L::GX, ly + kGY, y, a, h[0], h[1]);
+    load_site<P, PS>(bm, b0, bp, y, per, pull, g, v, h[0], h[1]);
     C drho[2], rho[2], jx[2], jy[2];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         drho[s] = sum9(h[s]);
-        rho[s] = a.k.rho_ref + drho[s];
+        rho[s] = v.rho_ref + drho[s];
         // sum_i w_i c_i = 0, so the offsets carry all of j
         const C d57 = h[s][5] - h[s][7], d68 = h[s][6] - h[s][8];
         jx[s] = (h[s][1] - h[s][3]) + (d57 - d68);
@@ -296,52 +280,51 @@ __device__ __forceinline__ void tile_body(const typename Prec<P>::T2* __restrict
     //               - (G_X/rho0) rho_s(r) sum_d w(d) d [rho_s'(r+d) - rho_s'(r-d)]
     // over one representative d of each +-d pair (the reference values cancel
     // in the differences); belt-1 and belt-2 pairs accumulate separately.
-    const int c0 = (ly + 2) * L::RX + (lx + 2);
     C axA1 = C(0), ayA1 = C(0), axB1 = C(0), ayB1 = C(0);
     C axA2 = C(0), ayA2 = C(0), axB2 = C(0), ayB2 = C(0);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-        const int dx = rdx(k), dy = rdy(k);
-        const C2 pp = spsi[c0 + dy * L::RX + dx], pm = spsi[c0 - dy * L::RX - dx];
+    for (int q = 0; q < 12; ++q) {
+        const int dx = rdx(q), dy = rdy(q);
+        const C2 pp = ps[2 + dy][dx], pm = ps[2 - dy][-dx];
         const C dA = pp.x - pm.x, dB = pp.y - pm.y;
-        C& axA = k < 4 ? axA1 : axA2;
-        C& ayA = k < 4 ? ayA1 : ayA2;
-        C& axB = k < 4 ? axB1 : axB2;
-        C& ayB = k < 4 ? ayB1 : ayB2;
+        C& axA = q < 4 ? axA1 : axA2;
+        C& ayA = q < 4 ? ayA1 : ayA2;
+        C& axB = q < 4 ? axB1 : axB2;
+        C& ayB = q < 4 ? ayB1 : ayB2;
         if (dx != 0) {
-            axA += (a.k.K[0][k] * C(dx)) * dA;
-            axB += (a.k.K[1][k] * C(dx)) * dB;
+            axA += (k.K[0][q] * C(dx)) * dA;
+            axB += (k.K[1][q] * C(dx)) * dB;
         }
         if (dy != 0) {
-            ayA += (a.k.K[0][k] * C(dy)) * dA;
-            ayB += (a.k.K[1][k] * C(dy)) * dB;
+            ayA += (k.K[0][q] * C(dy)) * dA;
+            ayB += (k.K[1][q] * C(dy)) * dB;
         }
     }
     C qxA = C(0), qyA = C(0), qxB = C(0), qyB = C(0);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int dx = rdx(k), dy = rdy(k);
-        const C2 rp = srho[c0 + dy * L::RX + dx], rm = srho[c0 - dy * L::RX - dx];
+    for (int q = 0; q < 4; ++q) {
+        const int dx = rdx(q), dy = rdy(q);
+        const C2 rp = rr[2 + dy][dx], rm = rr[2 - dy][-dx];
         const C dB = rp.y - rm.y, dA = rp.x - rm.x;   // A feels rho_B, B feels rho_A
         if (dx != 0) {
-            qxA += (a.k.W[k] * C(dx)) * dB;
-            qxB += (a.k.W[k] * C(dx)) * dA;
+            qxA += (k.W[q] * C(dx)) * dB;
+            qxB += (k.W[q] * C(dx)) * dA;
         }
         if (dy != 0) {
-            qyA += (a.k.W[k] * C(dy)) * dB;
-            qyB += (a.k.W[k] * C(dy)) * dA;
+            qyA += (k.W[q] * C(dy)) * dB;
+            qyB += (k.W[q] * C(dy)) * dA;
         }
     }
-    const C2 pc = spsi[c0];
-    const C pcA = a.k.psi_ref + pc.x, pcB = a.k.psi_ref + pc.y;
+    const C2 pc = ps[2][0];
+    const C pcA = v.psi_ref + pc.x, pcB = v.psi_ref + pc.y;
     C Fx[2], Fy[2];
-    Fx[0] = -pcA * (axA1 + axA2) - a.k.gx_rho0 * rho[0] * qxA;
-    Fy[0] = -pcA * (ayA1 + ayA2) - a.k.gx_rho0 * rho[0] * qyA;
-    Fx[1] = -pcB * (axB1 + axB2) - a.k.gx_rho0 * rho[1] * qxB;
-    Fy[1] = -pcB * (ayB1 + ayB2) - a.k.gx_rho0 * rho[1] * qyB;
-    if (GEN && a.k.has_accel) {
-        C acc = a.k.g_x;
-        if (a.k.kolmo_amp != C(0)) acc += a.k.kolmo_amp * csin(a.k.kolmo_w * C(y));
+    Fx[0] = -pcA * (axA1 + axA2) - v.gx_rho0 * rho[0] * qxA;
+    Fy[0] = -pcA * (ayA1 + ayA2) - v.gx_rho0 * rho[0] * qyA;
+    Fx[1] = -pcB * (axB1 + axB2) - v.gx_rho0 * rho[1] * qxB;
+    Fy[1] = -pcB * (ayB1 + ayB2) - v.gx_rho0 * rho[1] * qyB;
+    if (GEN && k.has_accel) {
+        C acc = k.g_x;
+        if (k.kolmo_amp != C(0)) acc += k.kolmo_amp * csin(k.kolmo_w * C(y));
         Fx[0] += rho[0] * acc;
         Fx[1] += rho[1] * acc;
     }
@@ -349,22 +332,22 @@ __device__ __forceinline__ void tile_body(const typename Prec<P>::T2* __restrict
     if (OBS) {
         const long long N = (long long)g.nx * g.ny;
         const long long idx = (long long)y * g.nx + x;
-        const double rA = (double)a.k.rho_ref + (double)drho[0];
-        const double rB = (double)a.k.rho_ref + (double)drho[1];
+        const double rA = (double)v.rho_ref + (double)drho[0];
+        const double rB = (double)v.rho_ref + (double)drho[1];
         const double tot = rA + rB;
         const double mx = (double)jx[0] + (double)jx[1] + 0.5 * ((double)Fx[0] + (double)Fx[1]);
         const double my = (double)jy[0] + (double)jy[1] + 0.5 * ((double)Fy[0] + (double)Fy[1]);
-        if (a.obs == OBS_FIELDS) {
-            a.obs_out[idx] = rA;
-            a.obs_out[N + idx] = rB;
-            a.obs_out[2 * N + idx] = tot != 0.0 ? mx / tot : 0.0;
-            a.obs_out[3 * N + idx] = tot != 0.0 ? my / tot : 0.0;
-        } else if (a.obs == OBS_POPS) {
+        if (o.obs == OBS_FIELDS) {
+            o.obs_out[idx] = rA;
+            o.obs_out[N + idx] = rB;
+            o.obs_out[2 * N + idx] = tot != 0.0 ? mx / tot : 0.0;
+            o.obs_out[3 * N + idx] = tot != 0.0 ? my / tot : 0.0;
+        } else if (o.obs == OBS_POPS) {
 #pragma unroll
             for (int q = 0; q < 18; ++q)
-                if (q >= a.q0 && q < a.q1)
-                    a.obs_out[(long long)(q - a.q0) * N + idx] =
-                        (double)h[q / 9][q % 9] + wgt<double>(q % 9) * (double)a.k.rho_ref;
+                if (q >= o.q0 && q < o.q1)
+                    o.obs_out[(long long)(q - o.q0) * N + idx] =
+                        (double)h[q / 9][q % 9] + wgt<double>(q % 9) * (double)v.rho_ref;
         }
         red[0] += rA;
         red[1] += rB;
@@ -375,27 +358,27 @@ __device__ __forceinline__ void tile_body(const typename Prec<P>::T2* __restrict
 
     // Eq. (1): forced BGK relaxation.  Common velocity
     // u' = sum_s (j_s/tau_s) / sum_s (rho_s/tau_s); shift u_s = u' + tau_s F_s/rho_s.
-    const C den = rho[0] * a.k.omega[0] + rho[1] * a.k.omega[1];
+    const C den = rho[0] * k.omega[0] + rho[1] * k.omega[1];
     C upx = C(0), upy = C(0);
     if (den != C(0)) {
         const C inv = recip(den);
-        upx = (jx[0] * a.k.omega[0] + jx[1] * a.k.omega[1]) * inv;
-        upy = (jy[0] * a.k.omega[0] + jy[1] * a.k.omega[1]) * inv;
+        upx = (jx[0] * k.omega[0] + jx[1] * k.omega[1]) * inv;
+        upy = (jy[0] * k.omega[0] + jy[1] * k.omega[1]) * inv;
     }
-    const bool source = GEN && a.k.source;
+    const bool source = GEN && k.source;
     C hs[2][9];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         C ux = upx, uy = upy;
         if (!source && rho[s] != C(0)) {
-            const C tr = a.k.tau[s] * recip(rho[s]);
+            const C tr = k.tau[s] * recip(rho[s]);
             ux += tr * Fx[s];
             uy += tr * Fy[s];
         }
         if (source)
-            collide<C, true>(h[s], hs[s], drho[s], rho[s], ux, uy, a.k.omega[s], Fx[s], Fy[s]);
+            collide<C, true>(h[s], hs[s], drho[s], rho[s], ux, uy, k.omega[s], Fx[s], Fy[s]);
         else
-            collide<C, false>(h[s], hs[s], drho[s], rho[s], ux, uy, a.k.omega[s], Fx[s], Fy[s]);
+            collide<C, false>(h[s], hs[s], drho[s], rho[s], ux, uy, k.omega[s], Fx[s], Fy[s]);
     }
     T2 e[9];
 #pragma unroll
@@ -403,49 +386,48 @@ __device__ __forceinline__ void tile_body(const typename Prec<P>::T2* __restrict
 
     // Full tiles go through the staging tile and a bulk tensor store; ragged
     // tiles and periodic ghost copies use plain stores.
-    const bool staged = stage != nullptr && x0 + L::TX <= g.nx && y0 + L::TY <= g.ny;
+    constexpr int TX = Prec<P>::TX, TY = Prec<P>::TY;
     const int dX = (x < 3) ? g.nx : ((x >= g.nx - 3) ? -g.nx : 0);
     long long dY = 0;
-    if (PER) dY = (y < 3) ? (long long)g.ny * g.pitch : ((y >= g.ny - 3) ? -(long long)g.ny * g.pitch : 0);
-    if (staged) {
+    if (per) dY = (y < 3) ? (long long)g.ny * g.pitch : ((y >= g.ny - 3) ? -(long long)g.ny * g.pitch : 0);
+    if (o.stage != nullptr) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) stage[(i * L::TY + ly) * L::TX + lx] = e[i];
+        for (int i = 0; i < 9; ++i) o.stage[i * TY * TX] = e[i];
     }
-    if (!staged || dX != 0 || dY != 0) {
+    if (o.stage == nullptr || dX != 0 || dY != 0) {
         const long long PL = (long long)g.rows * g.pitch;
-        T2* __restrict__ out =
-            reinterpret_cast<T2*>(a.fout) + (long long)(y + kGY) * g.pitch + (x + g.gx);
+        T2* __restrict__ out = o.fout + (long long)(y + kGY) * g.pitch + (x + g.gx);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            T2* o = out + i * PL;
-            if (!staged) o[0] = e[i];
-            if (dX) o[dX] = e[i];
+            T2* d = out + i * PL;
+            if (o.stage == nullptr) d[0] = e[i];
+            if (dX) d[dX] = e[i];
             if (dY) {
-                o[dY] = e[i];
-                if (dX) o[dY + dX] = e[i];
+                d[dY] = e[i];
+                if (dX) d[dY + dX] = e[i];
             }
         }
     }
-    if (!PER && (y == 0 || y == g.ny - 1)) {
+    if (!per && (y == 0 || y == g.ny - 1)) {
         // x-momentum handed to the wall by the links that will bounce back
         // at the next streaming: c_x (f*_i + f_opp), f_opp = f*_i - 6 w_i
         // rho_w (c_i . u_w), from the stored (rounded) values.
         const int down = (y == 0);
-        const C uw = down ? -a.k.u_wall : a.k.u_wall;
+        const C uw = down ? -v.u_wall : v.u_wall;
         C sA[9], sB[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const C2 v = dec2(e[i]);
-            sA[i] = v.x;
-            sB[i] = v.y;
+            const C2 q = dec2(e[i]);
+            sA[i] = q.x;
+            sB[i] = q.y;
         }
-        const C rw[2] = {a.k.rho_ref + sum9(sA), a.k.rho_ref + sum9(sB)};
+        const C rw[2] = {v.rho_ref + sum9(sA), v.rho_ref + sum9(sB)};
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             if ((down && cy(i) == -1) || (!down && cy(i) == 1)) {
 #pragma unroll
                 for (int s = 0; s < 2; ++s) {
-                    const C fi = (s ? sB[i] : sA[i]) + wgt<C>(i) * a.k.rho_ref;
+                    const C fi = (s ? sB[i] : sA[i]) + wgt<C>(i) * v.rho_ref;
                     const C back = fi - C(6) * wgt<C>(i) * rw[s] * (C(cx(i)) * uw);
                     const double dp = (double)(C(cx(i)) * (fi + back));
                     if (down) red[0] += dp; else red[1] += dp;
@@ -453,7 +435,6 @@ __device__ __forceinline__ void tile_body(const typename Prec<P>::T2* __restrict
             }
         }
     }
-    if (staged) fence_proxy_async();   // staging writes before the bulk store reads them
 }
 
 // FP64 block reduction of red[0..3] (all threads), result valid in thread 0.
@@ -477,151 +458,293 @@ __device__ __forceinline__ void block_sum4(double red[4], double (*s_red)[4]) {
     }
 }
 
-// Last-CTA pattern: every CTA has written its slot (thread 0); the CTA that
-// arrives last sums the `nslots` slots of `width` doubles in a fixed order.
-// Returns true in the last CTA, with the sums in red (valid in thread 0).
-template <int NT>
-__device__ __forceinline__ bool last_cta_sum(DevStats* st, const double* slots, int nslots,
-                                             int width, double red[4], double (*s_red)[4],
-                                             int* s_last) {
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        __threadfence();
-        const unsigned int tk = atomicAdd(&st->ticket, 1u);
-        *s_last = (tk == gridDim.x * gridDim.y - 1) ? 1 : 0;
-    }
-    __syncthreads();
-    if (!*s_last) return false;
-    __threadfence();
-    const volatile double* vs = slots;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int b = tid; b < nslots; b += NT)
-        for (int k = 0; k < width; ++k) v[k] += vs[width * b + k];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) red[k] = v[k];
-    block_sum4<NT>(red, s_red);
-    return true;
-}
-
 // ------------------------------------------------------------ step kernel
-// Persistent: one CTA per SM walks the tiles tile = blockIdx.x + k gridDim.x
-// (row-major tile order, so the CTAs in flight cover a narrow band of rows and
-// the halo overlap between tile rows is served by L2).  The box of the next
-// tile is loaded by TMA into the second buffer while the current tile is
-// computed; full tiles are written back by bulk tensor stores.
+// Persistent and multi-lattice.  The work items of a launch are segments of
+// TX-wide column strips, `seg` tiles (TY rows each) long, over all lattices
+// (segment-major within a lattice, so that the CTAs in flight cover a band
+// of rows and halo columns are shared through L2).  CTA b takes items
+// b, b + gridDim.x, ...  Walking down a strip, a CTA keeps the 8-row blocks
+// of f* (TMA-loaded into a ring of NB slots, one block ahead of use and
+// across item boundaries) and the density/Psi deviation rows (a ring of 16
+// rows), so each block is loaded and each deviation row computed once per
+// strip; only the x halo (4 of 72 columns) is redundant.  Full tiles are
+// written back by TMA bulk tensor stores.  The last CTA to finish advances
+// every lattice's step counter and buffer parity and takes the Couette wall
+// samples.
+// V: bit 0 = every lattice periodic (no wall code); bit 1 = general forcing.
 template <int P, int V>
 __global__ void __launch_bounds__(Layout<P>::NT, 1)
-    k_step(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
-           const __grid_constant__ StepArgs<typename Prec<P>::C> a) {
+    k_step(const __grid_constant__ BatchArgs<typename Prec<P>::C> a) {
     typedef Layout<P> L;
     typedef typename L::T2 T2;
+    typedef typename L::C C;
     typedef typename L::C2 C2;
+    constexpr bool ALLPER = (V & 1) != 0;
+    constexpr bool GEN = (V & 2) != 0;
+    constexpr int PS = L::TYB * L::BX;   // plane stride in a block slot (pairs)
     extern __shared__ unsigned char smem_raw[];
     // 128-byte aligned base, derived from the shared array by indexing so
     // that every access below compiles to shared-memory instructions.
     unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    auto box = [&](int b) { return reinterpret_cast<T2*>(smem + b * L::BOX_STRIDE); };
-    C2* srho = reinterpret_cast<C2*>(smem + 2 * L::BOX_STRIDE);   // [RY][RX]
-    C2* spsi = srho + L::RX * L::RY;                              // [RY][RX]
-    T2* stage = reinterpret_cast<T2*>(smem + L::STAGE_OFF);       // [9][TY][TX]
-    __shared__ __align__(8) uint64_t bars[2];
+    C2* ring_r = reinterpret_cast<C2*>(smem + L::RING_OFF);   // [RING][RX]
+    C2* ring_p = ring_r + L::RING * L::RX;                    // [RING][RX]
+    T2* stage = reinterpret_cast<T2*>(smem + L::STAGE_OFF);   // [9][TY][TX]
+    __shared__ __align__(8) uint64_t bars[L::NB];
     __shared__ int s_fail, s_last;
     __shared__ double s_red[L::NT / 32][4];
 
     const int tid = threadIdx.x;
-    const Geom& g = a.g;
-    const int ntx = (g.nx + L::TX - 1) / L::TX;
-    const int ntiles = ntx * ((g.ny + L::TY - 1) / L::TY);
+    const int G = gridDim.x;
+    auto slot = [&](int pos) { return reinterpret_cast<T2*>(smem + (pos % L::NB) * L::SLOT_BYTES); };
+    // descriptor of the lattice that owns work item it (descriptors sorted by item0)
+    auto find = [&](int it) {
+        int lo = 0, hi = a.nlat - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.lat[mid].item0 <= it) lo = mid; else hi = mid - 1;
+        }
+        return &a.lat[lo];
+    };
 
     if (tid == 0) {
         s_fail = 0;
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        for (int b = 0; b < L::NB; ++b) mbar_init(&bars[b], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    // Box origin in padded coordinates: site column x0 (= x0 - gx + gx), i.e.
-    // element 2 x0 of the interleaved rows, and row y0 (= y0 - 3 + kGY).
-    auto issue = [&](int tile, int b) {
-        const int x0 = (tile % ntx) * L::TX, y0 = (tile / ntx) * L::TY;
-        mbar_expect_tx(&bars[b], (uint32_t)L::BOX_BYTES);
-        tma_load_3d(box(b), &tin, 2 * x0, y0, 0, &bars[b]);
+
+    // Producer (thread 0): the blocks of this CTA's items, in order.  Item
+    // tiles [ty_a, ty_b) need blocks ty_a .. ty_b (block j = padded rows
+    // [8j, 8j + 8)); consecutive items' blocks follow each other.
+    int p_item = blockIdx.x, p_j = 0, p_pos = 0;
+    // cached geometry of the producer's current item
+    const CUtensorMap* p_map = nullptr;
+    int p_x0 = 0, p_ty_a = 0, p_nblk = 0;
+    auto p_load = [&]() {
+        if (p_item >= a.nitems) return;
+        const LatDesc<C>* d = find(p_item);
+        const int local = p_item - d->item0;
+        p_x0 = (local % d->nstrips) * L::TX;
+        p_ty_a = (local / d->nstrips) * d->seg;
+        p_nblk = min(p_ty_a + d->seg, d->ntiles_y) - p_ty_a + 1;
+        p_map = &d->tin[*((volatile int*)&d->st->cur)];
     };
-    if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+    auto issue_next = [&]() -> bool {
+        if (p_item >= a.nitems) return false;
+        uint64_t* bar = &bars[p_pos % L::NB];
+        mbar_expect_tx(bar, (uint32_t)L::SLOT_BYTES);
+        // box origin: pair column x0 (= x0 - gx + gx) -> element 2 x0; padded row 8j
+        tma_load_3d(slot(p_pos), p_map, 2 * p_x0, L::TYB * (p_ty_a + p_j), 0, bar);
+        ++p_pos;
+        if (++p_j == p_nblk) {
+            p_j = 0;
+            p_item += G;
+            p_load();
+        }
+        return true;
+    };
+    if (tid == 0) p_load();
+    if (tid == 0)
+        while (p_pos < L::NB && issue_next()) {}
 
     double red[4] = {0.0, 0.0, 0.0, 0.0};
     bool bad = false;
-    int k = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
-        const int b = k & 1;
-        if (tid == 0 && tile + (int)gridDim.x < ntiles) {
-            fence_proxy_async();   // earlier generic reads of box b^1 before the async write
-            issue(tile + gridDim.x, b ^ 1);
+    int c_pos = 0;   // ring position of the current item's first block
+    for (int it = blockIdx.x; it < a.nitems && !s_fail; it += G) {
+        const LatDesc<C>* d = find(it);
+        const int local = it - d->item0;
+        const int x0 = (local % d->nstrips) * L::TX;
+        const int ty_a = (local / d->nstrips) * d->seg;
+        const int ty_b = min(ty_a + d->seg, d->ntiles_y);
+        const Geom g = d->g;
+        const LatVals<C> v = d->v;
+        const bool per = ALLPER || g.periodic;
+        const int cur = *((volatile int*)&d->st->cur);
+        const int pull = *((volatile int*)&d->st->pull);
+        T2* fout = reinterpret_cast<T2*>(d->fbuf[cur ^ 1]);
+        auto rrow = [&](C2* ring, int y) { return ring + ((y + L::RING) & (L::RING - 1)) * L::RX; };
+        double wall[2] = {0.0, 0.0};
+        for (int ty = ty_a; ty < ty_b; ++ty) {
+            const int q = c_pos + (ty - ty_a);   // this tile uses blocks q and q + 1
+            // each thread sees the blocks land itself; a timeout is acted on
+            // after the next barrier (garbage read meanwhile is harmless)
+            if (!mbar_wait_bounded(&bars[q % L::NB], (q / L::NB) & 1) ||
+                !mbar_wait_bounded(&bars[(q + 1) % L::NB], ((q + 1) / L::NB) & 1))
+                s_fail = 1;
+            const int y0 = ty * L::TY;
+            // The tile's padded rows [8 ty, 8 ty + 16) are blocks q (slot s0) and
+            // q + 1 (slot s1); row pointers address plane 0.
+            const T2* s0 = slot(q);
+            const T2* s1 = slot(q + 1);
+            auto brow = [&](int R, int c) {
+                const int r = R - L::TYB * ty;
+                return (r < L::TYB ? s0 + r * L::BX : s1 + (r - L::TYB) * L::BX) + c;
+            };
+
+            // Phase 2: deviation rows new to this tile (all 12 at an item's start).
+            const int r_lo = (ty == ty_a) ? y0 - 2 : y0 + 2;
+            const int ncell = (y0 + L::TY + 2 - r_lo) * L::RX;
+            for (int c = tid; c < ncell; c += L::NT) {
+                const int ly = c / L::RX, lx = c - ly * L::RX;
+                const int y = r_lo + ly;
+                if (!per && (y < 0 || y >= g.ny)) continue;
+                const int bc = lx - 2 + L::GX;   // pair column in the block
+                const int R = y + kGY;
+                C2 r, p;
+                cell_dev<P, PS>(brow(R - 1, bc), brow(R, bc), brow(R + 1, bc), y, per, pull, g, v,
+                                r, p);
+                rrow(ring_r, y)[lx] = r;
+                rrow(ring_p, y)[lx] = p;
+            }
+            if (!per) {   // mirror the deviations about the halfway walls
+                __syncthreads();
+                for (int c = tid; c < ncell; c += L::NT) {
+                    const int ly = c / L::RX, lx = c - ly * L::RX;
+                    const int y = r_lo + ly;
+                    int ym;
+                    if (y < 0) ym = -1 - y;
+                    else if (y >= g.ny && y <= g.ny + 1) ym = 2 * g.ny - 1 - y;
+                    else continue;
+                    rrow(ring_r, y)[lx] = rrow(ring_r, ym)[lx];
+                    rrow(ring_p, y)[lx] = rrow(ring_p, ym)[lx];
+                }
+            }
+            if (tid == 0) bulk_wait_read();   // previous bulk store has read the staging tile
+            __syncthreads();
+            if (s_fail) break;
+
+            // Phase 3: one site per thread (lx < TX).
+            const bool full = x0 + L::TX <= g.nx && y0 + L::TY <= g.ny;
+            {
+                const int lx = tid % L::RX, ly = tid / L::RX;
+                const int x = x0 + lx, y = y0 + ly;
+                if (lx < L::TX && x < g.nx && y < g.ny) {
+                    const int bc = lx + L::GX;
+                    const int R = y + kGY;
+                    const C2* ps[5];
+                    const C2* rr[5];
+#pragma unroll
+                    for (int k2 = 0; k2 < 5; ++k2) {
+                        ps[k2] = rrow(ring_p, y + k2 - 2) + lx + 2;
+                        rr[k2] = rrow(ring_r, y + k2 - 2) + lx + 2;
+                    }
+                    SiteOut<T2> o;
+                    o.stage = full ? stage + ly * L::TX + lx : nullptr;
+                    o.fout = fout;
+                    o.obs = OBS_NONE;
+                    double wr[4] = {0.0, 0.0, 0.0, 0.0};
+                    site_update<P, false, GEN, PS>(brow(R - 1, bc), brow(R, bc), brow(R + 1, bc),
+                                                   ps, rr, x, y, per, pull, g, v, a.k, o, wr, bad);
+                    wall[0] += wr[0];
+                    wall[1] += wr[1];
+                    if (full) fence_proxy_async();   // staging writes before the bulk store
+                }
+            }
+            __syncthreads();
+            if (tid == 0) {
+                if (full) {
+                    // site (x0, y0) in padded coordinates: pair column x0 + gx, row y0 + kGY
+                    tma_store_3d(&d->tout[cur ^ 1], stage, 2 * (x0 + L::GX), y0 + kGY, 0);
+                    bulk_commit();
+                }
+                // blocks before the next tile's first block are free
+                const int released = (ty + 1 < ty_b) ? q + 1 : q + 2;
+                fence_proxy_async();   // generic reads of freed slots before async writes
+                while (p_pos < released + L::NB && issue_next()) {}
+            }
         }
-        if (!mbar_wait_bounded(&bars[b], (k >> 1) & 1)) s_fail = 1;
-        __syncthreads();
+        if (bad) {   // a density of this lattice went non-finite
+            atomicOr(&d->st->err, ERR_NONFINITE);
+            bad = false;
+        }
         if (s_fail) break;
-        const int x0 = (tile % ntx) * L::TX, y0 = (tile / ntx) * L::TY;
-        tile_body<P, false, V>(box(b), srho, spsi, x0, y0, a, red, bad, stage);
-        __syncthreads();
-        if (tid == 0 && x0 + L::TX <= g.nx && y0 + L::TY <= g.ny) {
-            // padded coordinates of site (x0, y0): pair column x0 + gx, row y0 + kGY
-            tma_store_3d(&tout, stage, 2 * (x0 + L::GX), y0 + kGY, 0);
-            bulk_commit();
+        c_pos += (ty_b - ty_a) + 1;
+        if (!per) {   // wall momentum of this item (zero unless it holds a wall row)
+            red[0] = wall[0];
+            red[1] = wall[1];
+            red[2] = red[3] = 0.0;
+            block_sum4<L::NT>(red, s_red);
+            if (tid == 0) {
+                a.slots[2 * it] = red[0];
+                a.slots[2 * it + 1] = red[1];
+            }
         }
     }
     if (tid == 0) bulk_wait_all();
-    if (s_fail) {
-        if (tid == 0) {
-            atomicOr(&a.st->err, ERR_TIMEOUT);
-            // let copies in flight land before the CTA exits
-            mbar_wait_bounded(&bars[k & 1], (k >> 1) & 1);
-            mbar_wait_bounded(&bars[(k + 1) & 1], ((k + 1) >> 1) & 1);
-        }
+    if (s_fail && tid == 0) {
+        // let copies in flight land before the CTA exits
+        for (int b = 0; b < L::NB; ++b) mbar_wait_bounded(&bars[b], 0), mbar_wait_bounded(&bars[b], 1);
     }
-    if (bad) atomicOr(&a.st->err, ERR_NONFINITE);
-    if (V & 1) return;   // periodic: no wall sums; the host keeps the step count
+    if (s_fail && tid == 0)   // report on every lattice of the launch
+        for (int l = 0; l < a.nlat; ++l) atomicOr(&a.lat[l].st->err, ERR_TIMEOUT);
 
-    // Couette: wall momentum of this step, then the last CTA samples it.
-    const long long t = *((volatile long long*)&a.st->t);
-    block_sum4<L::NT>(red, s_red);
+    // The last CTA advances every lattice and takes the wall samples.
     if (tid == 0) {
-        a.slots[2 * blockIdx.x] = red[0];
-        a.slots[2 * blockIdx.x + 1] = red[1];
-    }
-    if (!last_cta_sum<L::NT>(a.st, a.slots, gridDim.x, 2, red, s_red, &s_last)) return;
-    if (tid == 0) {
-        const long long every = a.stress_every > 0 ? a.stress_every : 1;
-        if (t >= a.stress_t0 && ((t - a.stress_t0) % every) == 0) {
-            a.st->sum_bot += red[0] / g.nx;
-            a.st->sum_top += red[1] / g.nx;
-            a.st->samples += 1;
-        }
-        a.st->t = t + 1;
-        a.st->ticket = 0u;
         __threadfence();
+        s_last = atomicAdd(a.ticket, 1u) == (unsigned int)(G - 1);
     }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int l = tid; l < a.nlat; l += L::NT) {
+        const LatDesc<C>* d = &a.lat[l];
+        DevStats* st = d->st;
+        const long long t = st->t;
+        if (!ALLPER && !d->g.periodic) {
+            const int n = d->nstrips * ((d->ntiles_y + d->seg - 1) / d->seg);
+            const volatile double* vs = a.slots + 2 * d->item0;
+            double sb = 0.0, stp = 0.0;
+            for (int i = 0; i < n; ++i) {
+                sb += vs[2 * i];
+                stp += vs[2 * i + 1];
+            }
+            const long long every = d->stress_every > 0 ? d->stress_every : 1;
+            if (t >= d->stress_t0 && ((t - d->stress_t0) % every) == 0) {
+                st->sum_bot += sb / d->g.nx;
+                st->sum_top += stp / d->g.nx;
+                st->samples += 1;
+            }
+        }
+        st->t = t + 1;
+        st->cur ^= 1;
+        st->pull = 1;
+    }
+    __threadfence();
+    if (tid == 0) *a.ticket = 0u;
 }
 
 // --------------------------------------------------------- observe kernel
-// One CTA per tile: fields, populations or totals of the current state.
+// One CTA per tile of one lattice: fields, populations or totals of the
+// current state, with the same site arithmetic as the step.
 template <int P, int V>
 __global__ void __launch_bounds__(Layout<P>::NT)
     k_observe(const __grid_constant__ CUtensorMap tin,
               const __grid_constant__ StepArgs<typename Prec<P>::C> a) {
     typedef Layout<P> L;
     typedef typename L::T2 T2;
+    typedef typename L::C C;
     typedef typename L::C2 C2;
+    constexpr bool GEN = (V & 2) != 0;
+    constexpr int PS = L::BY * L::BX;    // plane stride in the tile box (pairs)
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    T2* box = reinterpret_cast<T2*>(smem);
-    C2* srho = reinterpret_cast<C2*>(smem + L::BOX_STRIDE);
+    T2* box = reinterpret_cast<T2*>(smem);                    // [9][BY][BX]
+    C2* srho = reinterpret_cast<C2*>(smem + L::BOX_STRIDE);   // [RY][RX]
     C2* spsi = srho + L::RX * L::RY;
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_fail, s_last;
     __shared__ double s_red[L::NT / 32][4];
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * L::TX, y0 = blockIdx.y * L::TY;
+    const Geom& g = a.g;
+    const bool per = g.periodic != 0;
+    LatVals<C> v;
+    v.rho_ref = a.k.rho_ref;
+    v.psi_ref = a.k.psi_ref;
+    v.psi_scale = a.k.psi_scale;
+    v.inv_rho0 = a.k.inv_rho0;
+    v.gx_rho0 = a.k.gx_rho0;
+    v.u_wall = a.k.u_wall;
     if (tid == 0) {
         s_fail = 0;
         mbar_init(&bar, 1);
@@ -635,7 +758,54 @@ __global__ void __launch_bounds__(Layout<P>::NT)
     double red[4] = {0.0, 0.0, 0.0, 0.0};
     bool bad = false;
     if (!s_fail) {
-        tile_body<P, true, V>(box, srho, spsi, x0, y0, a, red, bad, nullptr);
+        // box row of lattice row y: y - y0 + kGY; deviation tile row: y - y0 + 2
+        for (int c = tid; c < L::RX * L::RY; c += L::NT) {
+            const int ly = c / L::RX, lx = c - ly * L::RX;
+            const int y = y0 - 2 + ly;
+            if (!per && (y < 0 || y >= g.ny)) continue;
+            const T2* b0 = box + (ly + 1) * L::BX + lx - 2 + L::GX;
+            C2 r, p;
+            cell_dev<P, PS>(b0 - L::BX, b0, b0 + L::BX, y, per, a.pull, g, v, r, p);
+            srho[ly * L::RX + lx] = r;
+            spsi[ly * L::RX + lx] = p;
+        }
+        if (!per) {
+            __syncthreads();
+            for (int c = tid; c < L::RX * L::RY; c += L::NT) {
+                const int ly = c / L::RX, lx = c - ly * L::RX;
+                const int y = y0 - 2 + ly;
+                int ym;
+                if (y < 0) ym = -1 - y;
+                else if (y >= g.ny) ym = 2 * g.ny - 1 - y;
+                else continue;
+                const int lm = ym - (y0 - 2);
+                if (lm < 0 || lm >= L::RY) continue;
+                srho[ly * L::RX + lx] = srho[lm * L::RX + lx];
+                spsi[ly * L::RX + lx] = spsi[lm * L::RX + lx];
+            }
+        }
+        __syncthreads();
+        const int lx = tid % L::RX, ly = tid / L::RX;
+        const int x = x0 + lx, y = y0 + ly;
+        if (lx < L::TX && x < g.nx && y < g.ny) {
+            const T2* b0 = box + (ly + kGY) * L::BX + lx + L::GX;
+            const C2* ps[5];
+            const C2* rr[5];
+#pragma unroll
+            for (int k2 = 0; k2 < 5; ++k2) {
+                ps[k2] = spsi + (ly + k2) * L::RX + lx + 2;
+                rr[k2] = srho + (ly + k2) * L::RX + lx + 2;
+            }
+            SiteOut<T2> o;
+            o.stage = nullptr;
+            o.fout = nullptr;
+            o.obs = a.obs;
+            o.obs_out = a.obs_out;
+            o.q0 = a.q0;
+            o.q1 = a.q1;
+            site_update<P, true, GEN, PS>(b0 - L::BX, b0, b0 + L::BX, ps, rr, x, y, per, a.pull, g,
+                                          v, a.k, o, red, bad);
+        }
     } else if (tid == 0) {
         atomicOr(&a.st->err, ERR_TIMEOUT);
         mbar_wait_bounded(&bar, 0);
@@ -643,11 +813,24 @@ __global__ void __launch_bounds__(Layout<P>::NT)
     if (bad) atomicOr(&a.st->err, ERR_NONFINITE);
     block_sum4<L::NT>(red, s_red);
     const int bid = blockIdx.y * gridDim.x + blockIdx.x;
-    if (tid == 0)
+    if (tid == 0) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) a.slots[4 * bid + q] = red[q];
-    if (!last_cta_sum<L::NT>(a.st, a.slots, gridDim.x * gridDim.y, 4, red, s_red, &s_last))
-        return;
+        __threadfence();
+        s_last = atomicAdd(&a.st->ticket, 1u) == gridDim.x * gridDim.y - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int nb = gridDim.x * gridDim.y;
+    const volatile double* vs = a.slots;
+    double w[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = tid; b < nb; b += L::NT)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] += vs[4 * b + q];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) red[q] = w[q];
+    block_sum4<L::NT>(red, s_red);
     if (tid == 0) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) a.st->totals[q] = red[q];
@@ -708,36 +891,50 @@ static cudaError_t configure(KS ks, KO ko) {
     return e;
 }
 
+// Opt every kernel of this precision into its dynamic shared memory, once
+// per device.
 template <int P>
-cudaError_t launch_step_prec(const CUtensorMap* tin, const CUtensorMap* tout, const void* args,
-                             int obs, dim3 grid, cudaStream_t s) {
-    typedef Layout<P> L;
-    typedef typename L::C C;
+static cudaError_t ensure_configured() {
     static int configured[64] = {0};
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 64 && !configured[dev]) {
-        cudaError_t e = configure<P>(k_step<P, 0>, k_observe<P, 2>);
-        if (e == cudaSuccess) e = configure<P>(k_step<P, 1>, k_observe<P, 3>);
-        if (e == cudaSuccess) e = configure<P>(k_step<P, 2>, k_observe<P, 2>);
-        if (e == cudaSuccess) e = configure<P>(k_step<P, 3>, k_observe<P, 3>);
-        if (e != cudaSuccess) return e;
-        configured[dev] = 1;
+    if (dev >= 0 && dev < 64 && configured[dev]) return cudaSuccess;
+    cudaError_t e = configure<P>(k_step<P, 0>, k_observe<P, 2>);
+    if (e == cudaSuccess) e = configure<P>(k_step<P, 1>, k_observe<P, 3>);
+    if (e == cudaSuccess) e = configure<P>(k_step<P, 2>, k_observe<P, 2>);
+    if (e == cudaSuccess) e = configure<P>(k_step<P, 3>, k_observe<P, 3>);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) configured[dev] = 1;
+    return e;
+}
+
+template <int P>
+cudaError_t launch_step_prec(const void* args, int variant, dim3 grid, cudaStream_t s) {
+    typedef Layout<P> L;
+    typedef typename L::C C;
+    cudaError_t e = ensure_configured<P>();
+    if (e != cudaSuccess) return e;
+    const BatchArgs<C>& a = *reinterpret_cast<const BatchArgs<C>*>(args);
+    switch (variant & 3) {
+        case 0: k_step<P, 0><<<grid, L::NT, L::SMEM, s>>>(a); break;
+        case 1: k_step<P, 1><<<grid, L::NT, L::SMEM, s>>>(a); break;
+        case 2: k_step<P, 2><<<grid, L::NT, L::SMEM, s>>>(a); break;
+        default: k_step<P, 3><<<grid, L::NT, L::SMEM, s>>>(a); break;
     }
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_observe_prec(const CUtensorMap* tin, const void* args, dim3 grid,
+                                cudaStream_t s) {
+    typedef Layout<P> L;
+    typedef typename L::C C;
+    cudaError_t e = ensure_configured<P>();
+    if (e != cudaSuccess) return e;
     const StepArgs<C>& a = *reinterpret_cast<const StepArgs<C>*>(args);
-    const int v = (a.g.periodic ? 1 : 0) | ((a.k.source || a.k.has_accel) ? 2 : 0);
-    if (obs == OBS_NONE) {
-        switch (v) {
-            case 0: k_step<P, 0><<<grid, L::NT, L::SMEM, s>>>(*tin, *tout, a); break;
-            case 1: k_step<P, 1><<<grid, L::NT, L::SMEM, s>>>(*tin, *tout, a); break;
-            case 2: k_step<P, 2><<<grid, L::NT, L::SMEM, s>>>(*tin, *tout, a); break;
-            default: k_step<P, 3><<<grid, L::NT, L::SMEM, s>>>(*tin, *tout, a); break;
-        }
-    } else if (a.g.periodic) {
+    if (a.g.periodic)
         k_observe<P, 3><<<grid, L::NT, L::SMEM_OBS, s>>>(*tin, a);
-    } else {
+    else
         k_observe<P, 2><<<grid, L::NT, L::SMEM_OBS, s>>>(*tin, a);
-    }
     return cudaGetLastError();
 }
 
@@ -759,8 +956,9 @@ cudaError_t launch_init_prec(const Geom& g, const void* coef, void* fout, int mo
 #ifndef LB_PREC
 #error "compile lb_kernels.cu once per storage precision with -DLB_PREC=0..3"
 #endif
-template cudaError_t launch_step_prec<LB_PREC>(const CUtensorMap*, const CUtensorMap*, const void*,
-                                               int, dim3, cudaStream_t);
+template cudaError_t launch_step_prec<LB_PREC>(const void*, int, dim3, cudaStream_t);
+template cudaError_t launch_observe_prec<LB_PREC>(const CUtensorMap*, const void*, dim3,
+                                                  cudaStream_t);
 template cudaError_t launch_init_prec<LB_PREC>(const Geom&, const void*, void*, int, const double*,
                                                double, double, double, int, unsigned long long,
                                                cudaStream_t);

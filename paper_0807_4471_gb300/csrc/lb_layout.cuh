@@ -41,21 +41,24 @@ __host__ __device__ constexpr int rdy(int k) {
 // as an interleaved pair (A, B), so that one vector access serves both.
 // T: stored scalar, T2: stored pair, C: compute scalar, C2: compute pair.
 template <int P> struct Prec;
+// TX: tile width, chosen so that a deviation row with its 2-cell halo,
+// TX + 4, is a multiple of 32 (one cell per thread); NB: ring slots of
+// 8-row population blocks in the step kernel.
 template <> struct Prec<LB_FP64> {
     typedef double T; typedef double2 T2; typedef double C; typedef double2 C2;
-    static constexpr int GX = 4, TX = 32, TY = 8;
+    static constexpr int GX = 4, TX = 28, TY = 8, NB = 3;
 };
 template <> struct Prec<LB_FP32> {
     typedef float T; typedef float2 T2; typedef float C; typedef float2 C2;
-    static constexpr int GX = 4, TX = 64, TY = 8;
+    static constexpr int GX = 4, TX = 60, TY = 8, NB = 4;
 };
 template <> struct Prec<LB_FP16_OFFSET> {
     typedef __half T; typedef __half2 T2; typedef float C; typedef float2 C2;
-    static constexpr int GX = 8, TX = 64, TY = 8;
+    static constexpr int GX = 8, TX = 60, TY = 8, NB = 4;
 };
 template <> struct Prec<LB_BF16_OFFSET> {
     typedef __nv_bfloat16 T; typedef __nv_bfloat162 T2; typedef float C; typedef float2 C2;
-    static constexpr int GX = 8, TX = 64, TY = 8;
+    static constexpr int GX = 8, TX = 60, TY = 8, NB = 4;
 };
 
 // Stored values are offsets h_i = f_i - w_i rho_ref from the lattice weights
@@ -108,23 +111,39 @@ struct Layout {
     typedef typename Prec<P>::T2 T2;
     typedef typename Prec<P>::C C;
     typedef typename Prec<P>::C2 C2;
-    static constexpr int TX = Prec<P>::TX, TY = Prec<P>::TY, NT = TX * TY;   // one site per thread
+    static constexpr int TX = Prec<P>::TX, TY = Prec<P>::TY;
     static constexpr int GX = Prec<P>::GX;
     static constexpr int BX = TX + 2 * GX;            // box columns (sites)
-    static constexpr int BY = TY + 2 * kGY;           // box rows
-    static constexpr int BOX_BYTES = 9 * BY * BX * (int)sizeof(T2);    // both species
-    static constexpr int BOX_STRIDE = (BOX_BYTES + 127) / 128 * 128;
+    static constexpr int BY = TY + 2 * kGY;           // observe box rows
     static constexpr int RX = TX + 4, RY = TY + 4;    // rho/Psi tile (2-cell halo)
+    // threads: one per deviation cell of a tile's 8 new rows; in the site
+    // phase thread (lx, ly) = (tid % RX, tid / RX) updates site lx < TX
+    static constexpr int NT = RX * TY;
+    static constexpr int TYB = 8;                     // rows of a step-kernel block
+    static constexpr int NB = Prec<P>::NB;            // ring slots of blocks
+    static constexpr int RING = 16;                   // rho/Psi ring rows (>= TY + 4 + TY/2)
+    // step kernel: NB block slots, the rho and Psi rings, the staging tile
+    static constexpr int SLOT_BYTES = 9 * TYB * BX * (int)sizeof(T2);
+    static constexpr int RING_OFF = NB * SLOT_BYTES;
+    static constexpr int RING_BYTES = 2 * RING * RX * (int)sizeof(C2);
+    static constexpr int STAGE_OFF = RING_OFF + RING_BYTES;
+    static constexpr int STAGE_BYTES = 9 * TY * TX * (int)sizeof(T2);
+    static constexpr int SMEM = STAGE_OFF + STAGE_BYTES + 128;
+    // observe kernel: one tile box and the rho/Psi tile
+    static constexpr int BOX_BYTES = 9 * BY * BX * (int)sizeof(T2);
+    static constexpr int BOX_STRIDE = (BOX_BYTES + 127) / 128 * 128;
     static constexpr int RHOPSI = (2 * RX * RY * (int)sizeof(C2) + 127) / 128 * 128;
-    static constexpr int STAGE_BYTES = 9 * TY * TX * (int)sizeof(T2);  // output tile
-    static constexpr int STAGE_OFF = 2 * BOX_STRIDE + RHOPSI;
-    static constexpr int SMEM = STAGE_OFF + STAGE_BYTES + 128;     // step: 2 boxes + staging
-    static constexpr int SMEM_OBS = BOX_STRIDE + RHOPSI + 128;     // observe: 1 box
-    static_assert(STAGE_BYTES % 128 == 0, "staging alignment");
+    static constexpr int SMEM_OBS = BOX_STRIDE + RHOPSI + 128;
+    static_assert(TY == TYB, "a tile spans one block plus the halo of the next");
+    static_assert(RX % 32 == 0, "deviation rows are whole warps");
+    static_assert((2 * TX * sizeof(T)) % 16 == 0 && (2 * (TX + GX) * sizeof(T)) % 16 == 0,
+                  "TMA x coordinates of tiles stay 16-byte aligned");
+    static_assert(SLOT_BYTES % 128 == 0 && RING_BYTES % 128 == 0 && STAGE_BYTES % 128 == 0,
+                  "128-byte alignment of the shared-memory regions");
     static_assert((BX * sizeof(T2)) % 16 == 0, "TMA box rows must be 16-byte multiples");
     static_assert(2 * BX <= 256 && 2 * TX <= 256 && BY <= 256, "TMA box extent");
     static_assert(GX >= 3 && (GX * sizeof(T)) % 16 == 0, "ghost width");
-    static_assert(SMEM <= 227 * 1024, "shared memory");
+    static_assert(SMEM <= 227 * 1024 - 1024 && SMEM_OBS <= 227 * 1024, "shared memory");
 };
 
 }  // namespace lbgb
