@@ -169,6 +169,62 @@ int64_t lb_time(const lb_handle* h);
 /* Release the handle (NULL is accepted).  Synchronises. */
 lb_status lb_destroy(lb_handle* h);
 
+/* ------------------------------------------------------------------------
+ * Lattice pool: many resident lattices stepped together, one persistent
+ * launch per time step over all active members (builder addition; the paper
+ * runs one lattice at a time, and its ensemble averages -- the overlap of
+ * Eq. (6) -- need many independent realisations).
+ *
+ * All members share the pool's precision, couplings (G_A1..G_X), tau_A,
+ * tau_B, psi_form, force_scheme and body forces; nx, ny, boundary, rho0,
+ * u_wall, init_amp, init_shear, rho_ref and the stress sampling vary per
+ * member.  Device memory is one arena of `bytes_budget` bytes allocated at
+ * creation; members are placed in it first-fit and admission fails with
+ * LB_ERR_NOMEM when a member's footprint does not fit.  Steps run on the
+ * pool's stream (a private stream is created when `stream` is NULL); runs of
+ * consecutive steps over an unchanged member set are captured once into a
+ * CUDA graph and replayed.  The work partition (segment length of the
+ * column strips) is tuned by timing candidate partitions on the first steps
+ * of each new member set (those steps are real steps) and cached.
+ * ------------------------------------------------------------------------ */
+typedef struct lb_pool lb_pool;
+typedef int32_t lb_job;
+
+/* Device bytes one member with parameters *p occupies in a pool arena. */
+lb_status lb_pool_footprint(const lb_params* p, size_t* bytes);
+
+lb_status lb_pool_create(const lb_params* shared, size_t bytes_budget, int32_t max_jobs,
+                         void* stream, lb_pool** out);
+
+/* Admit a member: place it in the arena, initialise it with lb_init_seeded's
+ * rule and `seed`, and schedule `steps` time steps.  *job receives its id.
+ * LB_ERR_NOMEM if it does not fit; LB_ERR_INVALID if the shared fields of *p
+ * differ from the pool's or the pool is full (max_jobs). */
+lb_status lb_pool_admit(lb_pool* pool, const lb_params* p, uint64_t seed, int64_t steps,
+                        lb_job* job);
+
+/* Advance every active member by min(quantum, its remaining steps); members
+ * that reach their step count drop out of the launches.  *active (may be
+ * NULL) receives the number of members with steps left afterwards.
+ * Asynchronous except for re-partitioning and tuning. */
+lb_status lb_pool_run(lb_pool* pool, int64_t quantum, int32_t* active);
+
+/* Steps done and whether the member has finished (all its steps). */
+lb_status lb_pool_poll(lb_pool* pool, lb_job job, int64_t* steps_done, int32_t* done);
+
+/* As lb_fields / lb_stress for one member (synchronise the pool stream). */
+lb_status lb_pool_fields(lb_pool* pool, lb_job job, double* rho_A, double* rho_B, double* ux,
+                         double* uy);
+lb_status lb_pool_stress(lb_pool* pool, lb_job job, lb_stress_out* out);
+
+/* Free a member's arena space (finished or not). */
+lb_status lb_pool_release(lb_pool* pool, lb_job job);
+
+/* Tiles per work item the current member set runs with (0 if none). */
+int32_t lb_pool_segment(const lb_pool* pool);
+
+lb_status lb_pool_destroy(lb_pool* pool);
+
 /* Largest lattice, nx * ny, that lb_totals_noalloc accepts (4096 x 4096). */
 #define LB_NOALLOC_MAX_SITES 16777216
 

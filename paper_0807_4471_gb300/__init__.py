@@ -94,6 +94,16 @@ def load():
             "lb_status_string": (C.c_char_p, [C.c_int]),
             "lb_totals_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+            "lb_pool_footprint": (C.c_int, [P, C.POINTER(C.c_size_t)]),
+            "lb_pool_create": (C.c_int, [P, C.c_size_t, C.c_int32, C.c_void_p, C.POINTER(H)]),
+            "lb_pool_admit": (C.c_int, [H, P, C.c_uint64, C.c_int64, C.POINTER(C.c_int32)]),
+            "lb_pool_run": (C.c_int, [H, C.c_int64, C.POINTER(C.c_int32)]),
+            "lb_pool_poll": (C.c_int, [H, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
+            "lb_pool_fields": (C.c_int, [H, C.c_int32, dp, dp, dp, dp]),
+            "lb_pool_stress": (C.c_int, [H, C.c_int32, C.POINTER(lb_stress_out)]),
+            "lb_pool_release": (C.c_int, [H, C.c_int32]),
+            "lb_pool_segment": (C.c_int32, [H]),
+            "lb_pool_destroy": (C.c_int, [H]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -184,6 +194,63 @@ def lb_destroy(h: int):
     _check(load().lb_destroy(C.c_void_p(h)), "lb_destroy")
 
 
+# ------------------------------------------------------------- lattice pool
+def lb_pool_footprint(p: lb_params) -> int:
+    n = C.c_size_t()
+    _check(load().lb_pool_footprint(C.byref(p), C.byref(n)), "lb_pool_footprint")
+    return n.value
+
+
+def lb_pool_create(shared: lb_params, budget: int, max_jobs: int, stream: int = 0) -> int:
+    h = C.c_void_p()
+    _check(load().lb_pool_create(C.byref(shared), budget, max_jobs, C.c_void_p(stream),
+                                 C.byref(h)), "lb_pool_create")
+    return h.value
+
+
+def lb_pool_admit(pool: int, p: lb_params, seed: int, steps: int) -> int:
+    j = C.c_int32()
+    _check(load().lb_pool_admit(C.c_void_p(pool), C.byref(p), seed, steps, C.byref(j)),
+           "lb_pool_admit")
+    return j.value
+
+
+def lb_pool_run(pool: int, quantum: int) -> int:
+    n = C.c_int32()
+    _check(load().lb_pool_run(C.c_void_p(pool), quantum, C.byref(n)), "lb_pool_run")
+    return n.value
+
+
+def lb_pool_poll(pool: int, job: int):
+    steps, done = C.c_int64(), C.c_int32()
+    _check(load().lb_pool_poll(C.c_void_p(pool), job, C.byref(steps), C.byref(done)),
+           "lb_pool_poll")
+    return steps.value, bool(done.value)
+
+
+def lb_pool_fields(pool: int, job: int, rho_A=None, rho_B=None, ux=None, uy=None):
+    _check(load().lb_pool_fields(C.c_void_p(pool), job, _dp(rho_A), _dp(rho_B), _dp(ux),
+                                 _dp(uy)), "lb_pool_fields")
+
+
+def lb_pool_stress(pool: int, job: int) -> dict:
+    out = lb_stress_out()
+    _check(load().lb_pool_stress(C.c_void_p(pool), job, C.byref(out)), "lb_pool_stress")
+    return {k: getattr(out, k) for k, _ in lb_stress_out._fields_}
+
+
+def lb_pool_release(pool: int, job: int):
+    _check(load().lb_pool_release(C.c_void_p(pool), job), "lb_pool_release")
+
+
+def lb_pool_segment(pool: int) -> int:
+    return load().lb_pool_segment(C.c_void_p(pool))
+
+
+def lb_pool_destroy(pool: int):
+    _check(load().lb_pool_destroy(C.c_void_p(pool)), "lb_pool_destroy")
+
+
 LB_NOALLOC_MAX_SITES = 16777216
 
 
@@ -269,6 +336,66 @@ class Lattice:
             lb_destroy(self.h)
             self.h = None
             self._ws = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Pool:
+    """Resident lattices stepped together (lb_pool_*).  `shared` fixes the
+    precision, couplings, tau, psi form and forcing of every member."""
+
+    def __init__(self, shared: lb_params, budget: int, max_jobs: int = 256, stream=None):
+        s = 0 if stream is None else stream.cuda_stream
+        self.h = lb_pool_create(shared, budget, max_jobs, s)
+        self.shared = shared
+        self._dims = {}
+
+    @staticmethod
+    def footprint(p: lb_params) -> int:
+        return lb_pool_footprint(p)
+
+    def admit(self, p: lb_params, seed: int, steps: int) -> int:
+        j = lb_pool_admit(self.h, p, seed, steps)
+        self._dims[j] = (p.ny, p.nx)
+        return j
+
+    def run(self, quantum: int) -> int:
+        return lb_pool_run(self.h, quantum)
+
+    def poll(self, job: int):
+        return lb_pool_poll(self.h, job)
+
+    def fields(self, job: int):
+        ny, nx = self._dims[job]
+        out = [np.empty((ny, nx)) for _ in range(4)]
+        lb_pool_fields(self.h, job, *out)
+        return out
+
+    def stress(self, job: int) -> dict:
+        return lb_pool_stress(self.h, job)
+
+    def release(self, job: int):
+        lb_pool_release(self.h, job)
+        self._dims.pop(job, None)
+
+    @property
+    def segment(self) -> int:
+        return lb_pool_segment(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lb_pool_destroy(self.h)
+            self.h = None
 
     def __enter__(self):
         return self

@@ -20,6 +20,7 @@ UNITS = [("lb_kernels.cu", [f"-DLB_PREC={p}"], f"lb_kernels_p{p}.o") for p in ra
     ("lb_dispatch.cu", [], "lb_dispatch.o"),
     ("lb_engine.cu", [], "lb_engine.o"),
     ("lb_api.cu", [], "lb_api.o"),
+    ("lb_pool.cu", [], "lb_pool.o"),
     ("lb_noalloc.cu", [], "lb_noalloc.o"),
 ]
 SOURCES = sorted({u[0] for u in UNITS})

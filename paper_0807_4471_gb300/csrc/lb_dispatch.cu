@@ -26,6 +26,11 @@ cudaError_t launch_step(int precision, const void* args, int variant, dim3 grid,
     return cudaErrorInvalidValue;
 }
 
+cudaError_t kernels_configure(int precision) {
+    LB_SWITCH(precision, return configure_prec<P>())
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_observe(int precision, const CUtensorMap* tin, const void* args, dim3 grid,
                            cudaStream_t s) {
     LB_SWITCH(precision, return launch_observe_prec<P>(tin, args, grid, s))

@@ -275,8 +275,15 @@ static void fill_desc(LatDesc<C>& d, const Lattice& L, const Coef<C>& k, int ite
     d.stress_t0 = L.p.stress_t0;
 }
 
+int launch_items(Lattice* const* lats, int nlat, int seg) {
+    int items = 0;
+    for (int l = 0; l < nlat; ++l) items += lats[l]->nstrips * ((lats[l]->ntiles_y + seg - 1) / seg);
+    return items;
+}
+
 lb_status launch_build(Launch& Ln, Lattice* const* lats, int nlat, void* descs, double* slots,
-                       unsigned int* ticket, int sms, cudaStream_t stream, void* host_scratch) {
+                       unsigned int* ticket, int sms, cudaStream_t stream, void* host_scratch,
+                       int forced_seg) {
     if (nlat < 1) return LB_ERR_INVALID;
     const int prec = lats[0]->p.precision;
     std::vector<int> ns((size_t)nlat), nt((size_t)nlat);
@@ -287,7 +294,7 @@ lb_status launch_build(Launch& Ln, Lattice* const* lats, int nlat, void* descs, 
         allper = allper && lats[l]->g.periodic;
         gen = gen || lats[l]->kd.source || lats[l]->kd.has_accel;
     }
-    const int seg = choose_seg(ns.data(), nt.data(), nlat, sms);
+    const int seg = forced_seg > 0 ? forced_seg : choose_seg(ns.data(), nt.data(), nlat, sms);
     int items = 0;
     const size_t dsz = prec == LB_FP64 ? sizeof(LatDesc<double>) : sizeof(LatDesc<float>);
     char* hs = reinterpret_cast<char*>(host_scratch);

@@ -56,9 +56,13 @@ int choose_seg(const int* nstrips, const int* ntiles_y, int nlat, int G);
 // Write the lattices' descriptors to `descs` (device, 128-byte aligned, room
 // for nlat LatDesc<double>) through `host_scratch` (as large, host) and fill
 // the launch.  Synchronises the stream.  All lattices share the precision
-// and the coefficients of lats[0] (couplings, tau, forcing).
+// and the coefficients of lats[0] (couplings, tau, forcing).  seg > 0 forces
+// the segment length; seg = 0 takes choose_seg's.
 lb_status launch_build(Launch& Ln, Lattice* const* lats, int nlat, void* descs, double* slots,
-                       unsigned int* ticket, int sms, cudaStream_t stream, void* host_scratch);
+                       unsigned int* ticket, int sms, cudaStream_t stream, void* host_scratch,
+                       int seg = 0);
+// Work items of a launch over lats with segment length seg.
+int launch_items(Lattice* const* lats, int nlat, int seg);
 lb_status launch_run(const Launch& Ln, cudaStream_t s);
 
 lb_status lattice_init_seeded(Lattice& L, uint64_t seed, cudaStream_t s);

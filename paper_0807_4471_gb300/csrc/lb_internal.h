@@ -134,6 +134,9 @@ int kernel_block_rows(int precision);
 // bit 0 = every lattice periodic, bit 1 = general forcing.  Observe: one
 // lattice, one CTA per tile (args: StepArgs<C>, tin: tile-box load map).
 cudaError_t launch_step(int precision, const void* args, int variant, dim3 grid, cudaStream_t s);
+// Opt the kernels of a precision into their shared memory (once per device;
+// call before capturing launches into a graph).
+cudaError_t kernels_configure(int precision);
 cudaError_t launch_observe(int precision, const CUtensorMap* tin, const void* args, dim3 grid,
                            cudaStream_t s);
 cudaError_t launch_init_seeded(int precision, const Geom& g, const void* coef, void* fout,
@@ -144,6 +147,8 @@ cudaError_t launch_init_fields(int precision, const Geom& g, const void* coef, v
 
 // Per-precision launchers, one explicit instantiation per compilation of
 // lb_kernels.cu (-DLB_PREC=P).
+template <int P>
+cudaError_t configure_prec();
 template <int P>
 cudaError_t launch_step_prec(const void* args, int variant, dim3 grid, cudaStream_t s);
 template <int P>

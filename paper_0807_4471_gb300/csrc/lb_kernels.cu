@@ -956,6 +956,12 @@ cudaError_t launch_init_prec(const Geom& g, const void* coef, void* fout, int mo
 #ifndef LB_PREC
 #error "compile lb_kernels.cu once per storage precision with -DLB_PREC=0..3"
 #endif
+template <int P>
+cudaError_t configure_prec() {
+    return ensure_configured<P>();
+}
+
+template cudaError_t configure_prec<LB_PREC>();
 template cudaError_t launch_step_prec<LB_PREC>(const void*, int, dim3, cudaStream_t);
 template cudaError_t launch_observe_prec<LB_PREC>(const CUtensorMap*, const void*, dim3,
                                                   cudaStream_t);
