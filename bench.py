@@ -237,6 +237,36 @@ def batched_mix(torch, lb, steps: int):
                 "GB_per_s_alg": sites * steps * 72 / dt / 1e9}
 
 
+def serving(torch, lb, njobs: int, step_scale: float, load: float, capacity_mlups: float):
+    """The served workload: the first `njobs` requests of the seeded arrival
+    stream (square lattices 64..2048, rho0 in [0.55, 0.83], shear rate 0 or
+    one of the 8 Couette rates), step counts scaled by `step_scale`, Poisson
+    arrivals at `load` x the measured batched capacity.  Jobs are served by
+    the continuous-batching server over a lattice pool (FP16 offsets)."""
+    from paper_0807_4471_gb300.serve import Server, job_params, percentile
+    specs = lbinputs.sample_serving()[:njobs]
+    for sp in specs:
+        sp["steps"] = max(10, int(round(sp["steps"] * step_scale)))
+    work = np.mean([sp["nx"] * sp["ny"] * sp["steps"] for sp in specs])
+    gap = work / (load * capacity_mlups * 1e6)          # mean inter-arrival time (s)
+    stream = [(sp["arrival"] * gap, sp) for sp in specs]
+    make = job_params(lb, dict(psi_form=lb.LB_PSI_RHO0), "fp16")
+    cuda_stream = torch.cuda.Stream()
+    budget = 48 << 30
+    pool = lb.Pool(make(dict(nx=64, ny=64)), budget, max_jobs=1024, stream=cuda_stream)
+    srv = Server(pool, make, quantum=200)
+    t0 = time.perf_counter()
+    jobs = srv.replay(stream)
+    makespan = time.perf_counter() - t0
+    pool.close()
+    lat = [j.latency for j in jobs if j.error is None]
+    return {"jobs": len(jobs), "failed": sum(1 for j in jobs if j.error), "p50_s": percentile(lat, 50),
+            "p99_s": percentile(lat, 99), "MLUPS": srv.stats.site_updates / makespan / 1e6,
+            "makespan_s": makespan, "step_scale": step_scale, "load": load,
+            "mean_interarrival_s": gap, "quantum": srv.quantum,
+            "refused_nomem": srv.stats.refused_nomem}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -249,6 +279,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-peak", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--lattices", type=int, default=len(lbinputs.CFG_SWEEP["rho0s"]),
                     help="number of sweep lattices stepped per bench step (profiling runs)")
     args = ap.parse_args()
@@ -359,6 +390,9 @@ def main():
             extra[f"peak_{p}_4096"] = {"MLUPS": mlups, "GB_per_s_alg": gbs,
                                        "frac_hbm": gbs / hbm_peak}
         extra["batched_64_fp16"] = batched_mix(torch, lb, 40)
+        if not args.no_serve:
+            extra["serving"] = serving(torch, lb, 300, 0.01, 0.8,
+                                       extra["batched_64_fp16"]["MLUPS"])
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
