@@ -345,6 +345,7 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "peak_kind": peak_kind,
                 "traffic": ncu_traffic("k_step", prec, f"{len(rho0s)}x{nx}x{ny}"),
+                "traffic_source": "profiles/traffic.json (ncu, taken on this kernel source)",
                 "bytes_per_launch_alg": BYTES_PER_SITE[prec] * sites,
                 "kernel": f"k_step<{prec}> (all {len(rho0s)} lattices per launch)",
                 "avg_launch_us": avg_launch * 1e6, "segment": pool.segment}
