@@ -125,6 +125,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(dist, value: float, device=None) -> float:
+    """The slowest rank's time (the bench's clock for N replicas)."""
+    import torch
+    if not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, world: int, seconds: float) -> float:
+    """Weak scaling: every rank runs the full workload; value = all ranks'
+    units / the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 def sweep_lattices(lb, precision: str, nx: int, ny: int, count: int):
     cfg = lbinputs.CFG_SWEEP
     lats = []
@@ -332,12 +348,9 @@ def main():
     barrier()
     for j in jobs:
         pool.stress(j)   # raises on a latched device error
-    if ws > 1:
-        t = torch.tensor([dt], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
+    dt = max_over_ranks(dist, dt, device="cuda")
     sites = nx * ny * len(rho0s)
-    value = sites * args.steps * ws / dt / 1e6
+    value = replica_throughput(sites * args.steps, ws, dt) / 1e6
     launches = args.steps          # one persistent launch per step for all lattices
     avg_launch = dt / launches
     hbm_peak, peak_kind = measured_peaks()
