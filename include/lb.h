@@ -141,6 +141,22 @@ lb_status lb_init_seeded(lb_handle* h, uint64_t seed);
 lb_status lb_init_fields(lb_handle* h, const double* rho_A, const double* rho_B,
                          const double* ux, const double* uy);
 
+/* Start from given populations f_is(r, t) [2][9][ny][nx] (host FP64, after
+ * streaming and before collision, as lb_populations writes them) at step
+ * t >= 0; the wall-stress averages restart.  Synchronises. */
+lb_status lb_init_populations(lb_handle* h, const double* f, int64_t t);
+
+/* Checkpoint / restart for long runs (the paper's runs reach 5e6 steps,
+ * text before Fig. 4).  lb_checkpoint writes the stored state as it is --
+ * [2][9][ny][nx] FP64 values f = stored offset + w_i rho_ref, the step count
+ * and `pulled` (1: the state is the post-collision f*(t-1); 0: f(t)) -- and
+ * lb_restore loads it into a handle with the same parameters.  The run then
+ * continues bitwise as the original for FP32/FP16/BF16 storage (FP64 offsets
+ * round-trip to within one ulp); wall-stress averages restart.  Both
+ * synchronise. */
+lb_status lb_checkpoint(lb_handle* h, double* state, int64_t* t, int32_t* pulled);
+lb_status lb_restore(lb_handle* h, const double* state, int64_t t, int32_t pulled);
+
 /* Advance n >= 0 time steps of Eq. (1) (asynchronous on the stream). */
 lb_status lb_step(lb_handle* h, int64_t n);
 

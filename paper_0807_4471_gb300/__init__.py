@@ -84,6 +84,9 @@ def load():
             "lb_create_in": (C.c_int, [P, C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(H)]),
             "lb_init_seeded": (C.c_int, [H, C.c_uint64]),
             "lb_init_fields": (C.c_int, [H, dp, dp, dp, dp]),
+            "lb_init_populations": (C.c_int, [H, dp, C.c_int64]),
+            "lb_checkpoint": (C.c_int, [H, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
+            "lb_restore": (C.c_int, [H, dp, C.c_int64, C.c_int32]),
             "lb_step": (C.c_int, [H, C.c_int64]),
             "lb_fields": (C.c_int, [H, dp, dp, dp, dp]),
             "lb_populations": (C.c_int, [H, dp]),
@@ -162,6 +165,21 @@ def lb_init_seeded(h: int, seed: int):
 def lb_init_fields(h: int, rho_A, rho_B, ux=None, uy=None):
     _check(load().lb_init_fields(C.c_void_p(h), _dp(rho_A), _dp(rho_B), _dp(ux), _dp(uy)),
            "lb_init_fields")
+
+
+def lb_init_populations(h: int, f, t: int):
+    _check(load().lb_init_populations(C.c_void_p(h), _dp(f), t), "lb_init_populations")
+
+
+def lb_checkpoint(h: int, state):
+    t, pulled = C.c_int64(), C.c_int32()
+    _check(load().lb_checkpoint(C.c_void_p(h), _dp(state), C.byref(t), C.byref(pulled)),
+           "lb_checkpoint")
+    return t.value, pulled.value
+
+
+def lb_restore(h: int, state, t: int, pulled: int):
+    _check(load().lb_restore(C.c_void_p(h), _dp(state), t, pulled), "lb_restore")
 
 
 def lb_step(h: int, n: int):
@@ -309,6 +327,20 @@ class Lattice:
 
     def step(self, n: int = 1):
         lb_step(self.h, n)
+        return self
+
+    def checkpoint(self):
+        """(stored state [2][9][ny][nx] FP64, step, pulled) -- see resume()."""
+        f = np.empty((2, 9, self.ny, self.nx))
+        t, pulled = lb_checkpoint(self.h, f)
+        return f, t, pulled
+
+    def resume(self, state, t: int, pulled: int):
+        lb_restore(self.h, np.ascontiguousarray(state, dtype=np.float64), t, pulled)
+        return self
+
+    def init_populations(self, f, t: int = 0):
+        lb_init_populations(self.h, np.ascontiguousarray(f, dtype=np.float64), t)
         return self
 
     def fields(self):

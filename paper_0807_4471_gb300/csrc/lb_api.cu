@@ -143,6 +143,25 @@ lb_status lb_init_fields(lb_handle* h, const double* rho_A, const double* rho_B,
     return lattice_init_fields(h->lat, rho_A, rho_B, ux, uy, h->stream);
 }
 
+lb_status lb_init_populations(lb_handle* h, const double* f, int64_t t) {
+    if (!h || !f) return LB_ERR_INVALID;
+    return lattice_load_populations(h->lat, f, t, 0, h->stream);
+}
+
+lb_status lb_checkpoint(lb_handle* h, double* state, int64_t* t, int32_t* pulled) {
+    if (!h || !state || !t || !pulled) return LB_ERR_INVALID;
+    if (!h->lat.inited) return LB_ERR_STATE;
+    lb_status s = lattice_populations(h->lat, state, h->stream, 1);
+    *t = h->lat.t;
+    *pulled = h->lat.pull;
+    return s;
+}
+
+lb_status lb_restore(lb_handle* h, const double* state, int64_t t, int32_t pulled) {
+    if (!h || !state) return LB_ERR_INVALID;
+    return lattice_load_populations(h->lat, state, t, pulled, h->stream);
+}
+
 lb_status lb_step(lb_handle* h, int64_t n) {
     if (!h || n < 0) return LB_ERR_INVALID;
     if (!h->lat.inited) return LB_ERR_STATE;

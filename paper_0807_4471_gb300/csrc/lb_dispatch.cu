@@ -51,6 +51,12 @@ cudaError_t launch_init_fields(int precision, const Geom& g, const void* coef, v
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_load_pops(int precision, const Geom& g, const void* coef, void* fout,
+                             const double* pops, int i0, int i1, cudaStream_t s) {
+    LB_SWITCH(precision, return launch_load_pops_prec<P>(g, coef, fout, pops, i0, i1, s))
+    return cudaErrorInvalidValue;
+}
+
 #undef LB_SWITCH
 
 }  // namespace lbgb

@@ -339,7 +339,14 @@ lb_status launch_run(const Launch& Ln, cudaStream_t s) {
     return cuda_status(launch_step(Ln.precision, args, Ln.variant, Ln.grid, s));
 }
 
+static lb_status lattice_observe_pull(Lattice& L, int obs, double* out, int q0, int q1, int pull,
+                                      cudaStream_t s);
 lb_status lattice_observe(Lattice& L, int obs, double* out, int q0, int q1, cudaStream_t s) {
+    return lattice_observe_pull(L, obs, out, q0, q1, L.pull, s);
+}
+
+static lb_status lattice_observe_pull(Lattice& L, int obs, double* out, int q0, int q1, int pull,
+                                      cudaStream_t s) {
     const int tx = kernel_tile_x(L.p.precision), ty = kernel_tile_y(L.p.precision);
     dim3 grid((unsigned)((L.p.nx + tx - 1) / tx), (unsigned)((L.p.ny + ty - 1) / ty), 1);
     cudaError_t e;
@@ -350,7 +357,7 @@ lb_status lattice_observe(Lattice& L, int obs, double* out, int q0, int q1, cuda
         a.k = L.kd;
         a.st = L.st;
         a.slots = L.slots;
-        a.pull = L.pull;
+        a.pull = pull;
         a.obs = obs;
         a.obs_out = out;
         a.q0 = q0;
@@ -363,7 +370,7 @@ lb_status lattice_observe(Lattice& L, int obs, double* out, int q0, int q1, cuda
         a.k = L.kf;
         a.st = L.st;
         a.slots = L.slots;
-        a.pull = L.pull;
+        a.pull = pull;
         a.obs = obs;
         a.obs_out = out;
         a.q0 = q0;
@@ -428,6 +435,35 @@ lb_status lattice_init_fields(Lattice& L, const double* rho_A, const double* rho
     return cuda_status(e);
 }
 
+lb_status lattice_load_populations(Lattice& L, const double* f, long long t, int pulled,
+                                   cudaStream_t s) {
+    if (t < 0 || (pulled != 0 && pulled != 1) || (pulled && t < 1)) return LB_ERR_INVALID;
+    lb_status st = lattice_reset(L, s);
+    if (st != LB_OK) return st;
+    const size_t n = (size_t)L.p.nx * L.p.ny;
+    // Stage whole directions (both species, 16 bytes per site) in buffer 1.
+    int per = (int)(L.fbytes / (n * 16));
+    if (per < 1) return LB_ERR_UNSUPPORTED;
+    double* stage = reinterpret_cast<double*>(L.fbuf[1]);
+    cudaError_t e = cudaSuccess;
+    for (int i0 = 0; i0 < 9 && e == cudaSuccess; i0 += per) {
+        const int i1 = i0 + per < 9 ? i0 + per : 9;
+        for (int i = i0; i < i1 && e == cudaSuccess; ++i)
+            for (int sp = 0; sp < 2 && e == cudaSuccess; ++sp)
+                e = cudaMemcpyAsync(stage + ((size_t)(i - i0) * 2 + sp) * n,
+                                    f + ((size_t)sp * 9 + i) * n, n * 8, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = launch_load_pops(L.p.precision, L.g, coef_ptr(L), L.fbuf[0], stage, i0, i1, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the stage is reused
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&L.st->t, &t, sizeof(long long), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&L.st->pull, &pulled, sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    L.t = t;
+    L.pull = pulled;
+    return LB_OK;
+}
+
 void lattice_advanced(Lattice& L, long long n) {
     if (n <= 0) return;
     L.t += n;
@@ -451,7 +487,7 @@ lb_status lattice_fields(Lattice& L, double* rho_A, double* rho_B, double* ux, d
     return lattice_read_stats(L, &ds, s);
 }
 
-lb_status lattice_populations(Lattice& L, double* f, cudaStream_t s) {
+lb_status lattice_populations(Lattice& L, double* f, cudaStream_t s, int raw) {
     const size_t n = (size_t)L.p.nx * L.p.ny;
     double* out = reinterpret_cast<double*>(L.fbuf[1 - L.cur]);
     int per = (int)(L.fbytes / (n * 8));
@@ -459,7 +495,7 @@ lb_status lattice_populations(Lattice& L, double* f, cudaStream_t s) {
     if (per > 18) per = 18;
     for (int q0 = 0; q0 < 18; q0 += per) {
         const int q1 = q0 + per < 18 ? q0 + per : 18;
-        lb_status st = lattice_observe(L, OBS_POPS, out, q0, q1, s);
+        lb_status st = lattice_observe_pull(L, OBS_POPS, out, q0, q1, raw ? 0 : L.pull, s);
         if (st != LB_OK) return st;
         cudaError_t e = cudaMemcpyAsync(f + (size_t)q0 * n, out, (size_t)(q1 - q0) * n * 8,
                                         cudaMemcpyDeviceToHost, s);

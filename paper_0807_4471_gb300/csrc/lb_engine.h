@@ -68,11 +68,19 @@ lb_status launch_run(const Launch& Ln, cudaStream_t s);
 lb_status lattice_init_seeded(Lattice& L, uint64_t seed, cudaStream_t s);
 lb_status lattice_init_fields(Lattice& L, const double* rho_A, const double* rho_B,
                               const double* ux, const double* uy, cudaStream_t s);
+// Resume from populations [2][9][ny][nx] (host FP64, as lattice_populations
+// writes them) at step t; stress averages restart.
+// pulled = 1: f holds the stored post-collision state f*(t-1) (a raw
+// checkpoint); 0: the populations f(t) before collision.
+lb_status lattice_load_populations(Lattice& L, const double* f, long long t, int pulled,
+                                   cudaStream_t s);
 void lattice_advanced(Lattice& L, long long n);
 lb_status lattice_observe(Lattice& L, int obs, double* out, int q0, int q1, cudaStream_t s);
 lb_status lattice_fields(Lattice& L, double* rho_A, double* rho_B, double* ux, double* uy,
                          cudaStream_t s);
-lb_status lattice_populations(Lattice& L, double* f, cudaStream_t s);
+// raw = 0: f(t) after streaming; raw = 1: the stored state as it is (f*(t-1)
+// when L.pull, else f(t)), for an exact checkpoint.
+lb_status lattice_populations(Lattice& L, double* f, cudaStream_t s, int raw = 0);
 lb_status lattice_stress(Lattice& L, lb_stress_out* out, cudaStream_t s);
 lb_status lattice_read_stats(Lattice& L, DevStats* out, cudaStream_t s);
 

@@ -145,6 +145,10 @@ cudaError_t launch_init_seeded(int precision, const Geom& g, const void* coef, v
 cudaError_t launch_init_fields(int precision, const Geom& g, const void* coef, void* fout,
                                const double* fields, cudaStream_t s);
 
+// Restore directions [i0, i1) from FP64 populations [i1 - i0][2][ny][nx].
+cudaError_t launch_load_pops(int precision, const Geom& g, const void* coef, void* fout,
+                             const double* pops, int i0, int i1, cudaStream_t s);
+
 // Per-precision launchers, one explicit instantiation per compilation of
 // lb_kernels.cu (-DLB_PREC=P).
 template <int P>
@@ -154,6 +158,9 @@ cudaError_t launch_step_prec(const void* args, int variant, dim3 grid, cudaStrea
 template <int P>
 cudaError_t launch_observe_prec(const CUtensorMap* tin, const void* args, dim3 grid,
                                 cudaStream_t s);
+template <int P>
+cudaError_t launch_load_pops_prec(const Geom& g, const void* coef, void* fout, const double* pops,
+                                  int i0, int i1, cudaStream_t s);
 template <int P>
 cudaError_t launch_init_prec(const Geom& g, const void* coef, void* fout, int mode,
                              const double* fields, double rho0, double amp, double u_wall,

@@ -881,6 +881,26 @@ __global__ void k_init(Geom g, Coef<typename Prec<P>::C> k, typename Prec<P>::T2
     }
 }
 
+// Restore directions [i0, i1) of a saved state: pops holds FP64 populations
+// f_is(r) of those directions as [i1 - i0][2][ny][nx]; the offsets
+// f - w_i rho_ref are encoded to the storage format (plus ghost copies).
+template <int P>
+__global__ void k_load_pops(Geom g, typename Prec<P>::C rho_ref, typename Prec<P>::T2* fout,
+                            const double* pops, int i0, int i1) {
+    typedef typename Prec<P>::T2 T2;
+    const long long N = (long long)g.nx * g.ny;
+    const double rref = (double)rho_ref;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(idx % g.nx), y = (int)(idx / g.nx);
+        for (int i = i0; i < i1; ++i) {
+            const double* src = pops + (long long)(i - i0) * 2 * N;
+            const double off = wgt<double>(i) * rref;
+            put2<T2>(fout, g, i, x, y, encd2<T2>(src[idx] - off, src[N + idx] - off));
+        }
+    }
+}
+
 // ------------------------------------------------------------- launchers
 template <int P, typename KS, typename KO>
 static cudaError_t configure(KS ks, KO ko) {
@@ -965,6 +985,21 @@ template cudaError_t configure_prec<LB_PREC>();
 template cudaError_t launch_step_prec<LB_PREC>(const void*, int, dim3, cudaStream_t);
 template cudaError_t launch_observe_prec<LB_PREC>(const CUtensorMap*, const void*, dim3,
                                                   cudaStream_t);
+template <int P>
+cudaError_t launch_load_pops_prec(const Geom& g, const void* coef, void* fout, const double* pops,
+                                  int i0, int i1, cudaStream_t s) {
+    typedef typename Prec<P>::C C;
+    typedef typename Prec<P>::T2 T2;
+    const long long N = (long long)g.nx * g.ny;
+    long long blocks = (N + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    k_load_pops<P><<<(unsigned)blocks, 256, 0, s>>>(
+        g, reinterpret_cast<const Coef<C>*>(coef)->rho_ref, reinterpret_cast<T2*>(fout), pops, i0, i1);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_load_pops_prec<LB_PREC>(const Geom&, const void*, void*, const double*,
+                                                    int, int, cudaStream_t);
 template cudaError_t launch_init_prec<LB_PREC>(const Geom&, const void*, void*, int, const double*,
                                                double, double, double, int, unsigned long long,
                                                cudaStream_t);

@@ -238,3 +238,48 @@ def test_half_offset_20_steps(lb, O, fmt, tol):
     print(f"{fmt} 20-step relative error {err:.3e}")
     assert err < tol
     g.close()
+
+
+# ------------------------------------------------------ checkpoint / resume
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("boundary", [0, 1])
+def test_checkpoint_restore(lb, prec, boundary):
+    """lb_checkpoint at step 30 and lb_restore into a fresh handle continue
+    exactly like the original run (bitwise for FP32/FP16/BF16 storage; FP64
+    offsets round-trip to an ulp)."""
+    m = model(96, 64, boundary=boundary, u_wall=0.02 if boundary else 0.0)
+    g = lb.Lattice(gpu_params(lb, m, prec)).init_seeded(5)
+    g.step(30)
+    state, t, pulled = g.checkpoint()
+    assert (t, pulled) == (30, 1)
+    f30 = g.populations()
+    g.step(40)
+    a = g.fields()
+    h = lb.Lattice(gpu_params(lb, m, prec)).resume(state, t, pulled)
+    assert h.t == 30
+    assert rel_err(h.populations(), f30) <= (1e-15 if prec == "fp64" else 0.0)
+    h.step(40)
+    b = h.fields()
+    assert h.t == 70
+    for x, y in zip(a, b):
+        if prec == "fp64":
+            assert np.abs(x - y).max() <= 1e-12 * max(1.0, np.abs(y).max())
+        else:
+            assert np.array_equal(x, y)
+    g.close()
+    h.close()
+
+
+def test_init_populations_from_oracle(lb, O):
+    """Start from populations given on the host (here the oracle's state at
+    step 20) and continue: matches the oracle's continuation (FP64)."""
+    m = model(48, 40, boundary=1, u_wall=0.02)
+    P = oracle_params(O, m)
+    f = O.init_seeded(P, 2)
+    O.run(P, f, 20)
+    g = lb.Lattice(gpu_params(lb, m, "fp64")).init_populations(f.transpose(2, 3, 0, 1), 20)
+    assert g.t == 20
+    O.run(P, f, 30, t0=20)
+    g.step(30)
+    assert rel_err(gpu_pops_as_oracle(g.populations()), f) < 1e-12
+    g.close()
