@@ -1,0 +1,202 @@
+"""Observables and experiments of the paper, run on the GPU library.
+
+* structure_factor: radially binned S(k) of phi = rho_A - rho_B (the measure
+  used to compare long chaotic runs statistically).
+* interface_indicator: I_AB = sum_r grad rho_A . grad rho_B (text before
+  Fig. 3), with central differences on the periodic lattice.
+* kolmogorov_run: the shear experiment of the paper (forcing that sustains
+  U_x = U0 sin(k y) in a Newtonian fluid), returning the response
+  R(t) = U(t)/U0 and I_AB(t) (Fig. 3).
+* ageing_overlap: C(t_w, tau) of Eq. (6) over an ensemble of realisations,
+  stepped together in one lattice pool (Fig. 4).
+* laplace_test: surface tension from the pressure jump across the
+  interface of a circular drop, sigma = R (p_in - p_out) (Fig. 2, left).
+* couette_study: time-averaged wall stress and effective viscosity of plane
+  Couette runs over shear rates and storage precisions.
+
+The host code here only samples fields (lb_fields) and reduces them with
+numpy; every time step runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+CS2 = 1.0 / 3.0
+
+
+# ---------------------------------------------------------------- measures
+def structure_factor(phi: np.ndarray):
+    """S(k) = |FFT(phi - <phi>)|^2 / N, averaged over rings of width 2 pi / L
+    (L = min(nx, ny)).  Returns (k centres, S per ring, modes per ring)."""
+    ny, nx = phi.shape
+    f = np.fft.fft2(phi - phi.mean())
+    s = (np.abs(f) ** 2) / phi.size
+    kx = 2 * np.pi * np.fft.fftfreq(nx)
+    ky = 2 * np.pi * np.fft.fftfreq(ny)
+    kk = np.sqrt(kx[None, :] ** 2 + ky[:, None] ** 2)
+    dk = 2 * np.pi / min(nx, ny)
+    idx = np.floor(kk / dk + 0.5).astype(int)
+    nb = idx.max() + 1
+    tot = np.bincount(idx.ravel(), weights=s.ravel(), minlength=nb)
+    cnt = np.bincount(idx.ravel(), minlength=nb)
+    with np.errstate(invalid="ignore"):
+        avg = np.where(cnt > 0, tot / np.maximum(cnt, 1), 0.0)
+    return np.arange(nb) * dk, avg, cnt
+
+
+def domain_length(phi: np.ndarray) -> float:
+    """Characteristic domain size 2 pi sum S / sum k S (k > 0)."""
+    k, s, c = structure_factor(phi)
+    w = s * c
+    return float(2 * np.pi * w[1:].sum() / (k[1:] * w[1:]).sum())
+
+
+def interface_indicator(rho_a: np.ndarray, rho_b: np.ndarray) -> float:
+    """I_AB = sum grad rho_A . grad rho_B, central differences, periodic."""
+    def grad(f):
+        return ((np.roll(f, -1, 1) - np.roll(f, 1, 1)) / 2, (np.roll(f, -1, 0) - np.roll(f, 1, 0)) / 2)
+    ax, ay = grad(rho_a)
+    bx, by = grad(rho_b)
+    return float((ax * bx + ay * by).sum())
+
+
+def sine_projection(ux: np.ndarray, kmode: int = 1) -> float:
+    """Amplitude U of u_x = U sin(2 pi kmode y / ny): 2 <u_x sin(k y)>."""
+    ny = ux.shape[0]
+    s = np.sin(2 * np.pi * kmode * np.arange(ny) / ny)[:, None]
+    return float(2 * (ux * s).mean())
+
+
+def bulk_pressure(rho_a, rho_b, Ga, Gr, GX, rho0, psi_pref):
+    """Bulk part of Eq. (3): c_s^2 (rho_A + rho_B) + (c_s^2/2) sum_s
+    (G^a_s + G^r_s) Psi_s^2 + c_s^2 (G_X/rho0) rho_A rho_B."""
+    pa = psi_pref * (1 - np.exp(-rho_a / rho0))
+    pb = psi_pref * (1 - np.exp(-rho_b / rho0))
+    return (CS2 * (rho_a + rho_b) + 0.5 * CS2 * ((Ga[0] + Gr[0]) * pa ** 2 + (Ga[1] + Gr[1]) * pb ** 2)
+            + CS2 * (GX / rho0) * rho_a * rho_b)
+
+
+def overlap(phi_w: np.ndarray, phi_t: np.ndarray) -> float:
+    """One realisation's numerator and denominator of Eq. (6)."""
+    return float((phi_w * phi_t).sum()), float((phi_w * phi_w).sum())
+
+
+# -------------------------------------------------------------- experiments
+def kolmogorov_run(lb, n: int = 128, U0: float = 0.1, steps: int = 2000, every: int = 100,
+                   seed: int = 0, precision: str = "fp32", **kw):
+    """Shear by the body force a_x(y) = nu0 k^2 U0 sin(k y), k = 2 pi / n,
+    which sustains U_x = U0 sin(k y) in a fluid of viscosity nu0 =
+    c_s^2 (tau - 1/2).  Returns [(t, R, I_AB)], R = U(t)/U0."""
+    tau = kw.pop("tau_A", 1.0)
+    nu0 = CS2 * (tau - 0.5)
+    k = 2 * np.pi / n
+    p = lb.make_params(n, n, precision, tau_A=tau, tau_B=kw.pop("tau_B", tau),
+                       kolmo_amp=nu0 * k * k * U0, kolmo_k=1.0, **kw)
+    out = []
+    with lb.Lattice(p) as g:
+        g.init_seeded(seed)
+        for t in range(0, steps + 1, every):
+            if t:
+                g.step(every)
+            ra, rb, ux, _ = g.fields()
+            out.append((t, sine_projection(ux) / U0, interface_indicator(ra, rb)))
+    return out
+
+
+def ageing_overlap(lb, n: int, seeds, t_w: int, taus, precision: str = "fp16", U0: float = 0.0,
+                   **kw):
+    """C(t_w, tau) of Eq. (6): ensemble averages over `seeds` of
+    sum phi(t_w) phi(t_w + tau) / sum phi(t_w)^2, with the realisations
+    stepped together in one pool.  U0 > 0 adds the Kolmogorov forcing."""
+    nu0 = CS2 * (kw.get("tau_A", 1.0) - 0.5)
+    k = 2 * np.pi / n
+    extra = dict(kolmo_amp=nu0 * k * k * U0, kolmo_k=1.0) if U0 else {}
+    p = lb.make_params(n, n, precision, **kw, **extra)
+    taus = sorted(int(x) for x in taus)
+    total = t_w + taus[-1]
+    budget = lb.Pool.footprint(p) * len(seeds) + (64 << 20)
+    num = np.zeros(len(taus))
+    den = 0.0
+    with lb.Pool(p, budget, max_jobs=len(seeds)) as pool:
+        jobs = [pool.admit(p, int(s), total) for s in seeds]
+        pool.run(t_w)
+        phi_w = []
+        for j in jobs:
+            ra, rb, _, _ = pool.fields(j)
+            phi_w.append(ra - rb)
+            den += float((phi_w[-1] ** 2).sum())
+        t = t_w
+        for i, tau in enumerate(taus):
+            pool.run(t_w + tau - t)
+            t = t_w + tau
+            for j, pw in zip(jobs, phi_w):
+                ra, rb, _, _ = pool.fields(j)
+                num[i] += float((pw * (ra - rb)).sum())
+    return taus, num / den
+
+
+def drop_fields(n: int, radius: float, rho_in, rho_out):
+    """A circular drop of species A (densities rho_in = (A, B) inside,
+    rho_out outside) centred on an n x n lattice, with a tanh profile."""
+    y, x = np.mgrid[0:n, 0:n]
+    r = np.sqrt((x - n / 2 + 0.5) ** 2 + (y - n / 2 + 0.5) ** 2)
+    s = 0.5 * (1 - np.tanh((r - radius) / 2.0))
+    ra = rho_out[0] + (rho_in[0] - rho_out[0]) * s
+    rb = rho_out[1] + (rho_in[1] - rho_out[1]) * s
+    return ra, rb
+
+
+def laplace_test(lb, rho0: float, radii=(12, 16, 24), n: int = 96, steps: int = 20000,
+                 precision: str = "fp32", psi_form: int = 1, **kw):
+    """Equilibrate drops of A in B and fit p_in - p_out = sigma / R (2-D
+    Laplace law) with the bulk pressure of Eq. (3).  Returns (sigma, rows of
+    (R measured, dp))."""
+    c = dict(kw)
+    p = lb.make_params(n, n, precision, rho0=rho0, psi_form=psi_form, **c)
+    Ga, Gr = (p.G_A1, p.G_B1), (p.G_A2, p.G_B2)
+    pref = rho0 if psi_form == 1 else math.sqrt(rho0)
+    rows = []
+    for R in radii:
+        ra, rb = drop_fields(n, R, (1.6 * rho0, 0.1 * rho0), (0.1 * rho0, 1.6 * rho0))
+        with lb.Lattice(p) as g:
+            g.init_fields(ra, rb)
+            g.step(steps)
+            fa, fb, _, _ = g.fields()
+        pr = bulk_pressure(fa, fb, Ga, Gr, p.G_X, rho0, pref)
+        c0 = n // 2
+        p_in = float(pr[c0 - 2:c0 + 2, c0 - 2:c0 + 2].mean())
+        p_out = float(np.concatenate([pr[:3].ravel(), pr[-3:].ravel()]).mean())
+        phi = fa - fb
+        area = float((phi > 0).sum())
+        rows.append((math.sqrt(area / math.pi), p_in - p_out))
+    x = np.array([1.0 / r for r, _ in rows])
+    yv = np.array([d for _, d in rows])
+    sigma = float((x * yv).sum() / (x * x).sum())
+    return sigma, rows
+
+
+def couette_study(lb, rates, precisions=("fp32", "fp16", "bf16"), n: int = 512,
+                  steps: int = 200_000, avg_from: int = 100_000, rho0: float = 0.70,
+                  seed: int = 2, **kw):
+    """Time-averaged wall stress and effective viscosity of plane Couette
+    runs (walls at +-U, shear rate 2U/n) for each storage precision; the
+    lattices of one precision run together in one pool.  Returns
+    {precision: [dict(rate, sigma, nu_eff, R)]}."""
+    out = {}
+    for prec in precisions:
+        ps = [lb.make_params(n, n, prec, boundary=1, u_wall=r * n / 2.0, init_shear=1,
+                             rho0=rho0, stress_t0=avg_from, **kw) for r in rates]
+        budget = sum(lb.Pool.footprint(p) for p in ps) + (64 << 20)
+        with lb.Pool(ps[0], budget, max_jobs=len(ps)) as pool:
+            jobs = [pool.admit(p, seed, steps) for p in ps]
+            while pool.run(10_000):
+                pass
+            rows = []
+            for r, j in zip(rates, jobs):
+                st = pool.stress(j)
+                rows.append(dict(rate=r, sigma=st["sigma_mean"], nu_eff=st["nu_eff"],
+                                 R=st["response_R"], samples=st["samples"]))
+        out[prec] = rows
+    return out

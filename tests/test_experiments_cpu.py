@@ -1,0 +1,80 @@
+"""Observables of the experiments module against closed forms, and the
+oracle against two physical facts they rely on: the steady Kolmogorov
+amplitude of a passive fluid, and mechanical equilibrium (equal bulk
+pressure of Eq. (3)) across a flat A/B interface."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_0807_4471_gb300 import experiments as E
+
+
+def test_structure_factor_parseval_and_peak():
+    n = 64
+    y, x = np.mgrid[0:n, 0:n]
+    phi = 0.3 * np.cos(2 * np.pi * 5 * x / n) + 0.1 * np.sin(2 * np.pi * 3 * y / n) + 0.7
+    k, s, c = E.structure_factor(phi)
+    assert abs((s * c).sum() - ((phi - phi.mean()) ** 2).sum()) < 1e-9
+    top = np.argsort(s * c)[-2:]
+    assert set(top) == {3, 5}
+    assert abs(k[5] - 2 * np.pi * 5 / n) < 1e-12
+    assert (s * c)[5] == pytest.approx(2 * n * n * 0.3 ** 2 / 4, rel=1e-12)
+
+
+def test_interface_indicator_closed_form():
+    n, m = 48, 3
+    q = 2 * np.pi * m / n
+    x = np.arange(n)
+    a = np.tile(np.cos(q * x), (n, 1))
+    b = np.tile(-2 * np.cos(q * x), (n, 1))
+    # central differences: d/dx cos(q x) -> -sin(q) sin(q x)
+    want = -2 * n * n * math.sin(q) ** 2 / 2
+    assert E.interface_indicator(a, b) == pytest.approx(want, rel=1e-12)
+
+
+def test_sine_projection_and_overlap():
+    ny = 40
+    ux = 0.07 * np.sin(2 * np.pi * np.arange(ny) / ny)[:, None] * np.ones((1, 12)) + 0.01
+    assert E.sine_projection(ux) == pytest.approx(0.07, rel=1e-12)
+    phi = np.random.default_rng(1).standard_normal((16, 16))
+    num, den = E.overlap(phi, phi)
+    assert num == den
+    num, den = E.overlap(phi, -phi)
+    assert num == -den
+
+
+def test_kolmogorov_steady_amplitude_oracle(O):
+    """Passive two-species fluid (all G = 0) forced by a_x = nu0 k^2 U0 sin(ky):
+    the steady amplitude is U0 (R = 1) up to the lattice error O(k^2)."""
+    n, U0, tau = 32, 0.01, 1.0
+    nu0 = (tau - 0.5) / 3
+    k = 2 * np.pi / n
+    P = O.make_params(4, n, Ga=(0.0, 0.0), Gr=(0.0, 0.0), GX=0.0, rho0=0.5, init_amp=0.0,
+                      kolmo_amp=nu0 * k * k * U0, kolmo_k=1.0)
+    f = O.init_seeded(P, 0)
+    O.run(P, f, 12000)
+    _, _, ux, _ = O.fields(P, f)
+    R = E.sine_projection(ux) / U0
+    assert abs(R - 1.0) < 0.01
+
+
+def test_flat_interface_pressure_balance_oracle(O, caption):
+    """A flat A/B interface relaxes to mechanical equilibrium: the bulk
+    pressure of Eq. (3) is the same in the A-rich and the B-rich phase."""
+    nx, ny = 4, 64
+    y = np.arange(ny)[:, None].repeat(nx, 1)
+    s = 0.5 * (1 + np.tanh((np.minimum(y - 16, 48 - y)) / 2.0))
+    r0 = caption["rho0"]
+    ra = 0.1 * r0 + 1.5 * r0 * s
+    rb = 1.6 * r0 - 1.5 * r0 * s
+    P = O.make_params(nx, ny, **caption, psi_form=1)
+    f = O.init_fields(P, ra, rb)
+    O.run(P, f, 6000)
+    fa, fb, ux, uy = O.fields(P, f)
+    p = E.bulk_pressure(fa, fb, caption["Ga"], caption["Gr"], caption["GX"], r0, r0)
+    p_a, p_b = p[32, 0], p[0, 0]
+    assert fa[32, 0] > fb[32, 0] and fb[0, 0] > fa[0, 0]      # two bulk phases
+    assert abs(p_a - p_b) < 2e-3 * abs(p_a)
+    # spurious currents at the interface stay small (1e-6 here)
+    assert np.abs(ux).max() < 1e-5 and np.abs(uy).max() < 1e-5
