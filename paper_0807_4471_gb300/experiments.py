@@ -10,7 +10,7 @@
 * ageing_overlap: C(t_w, tau) of Eq. (6) over an ensemble of realisations,
   stepped together in one lattice pool (Fig. 4).
 * laplace_test: surface tension from the pressure jump across the
-  interface of a circular drop, sigma = R (p_in - p_out) (Fig. 2, left).
+  interface of circular drops, p_in - p_out = sigma / R (Fig. 2, left).
 * couette_study: time-averaged wall stress and effective viscosity of plane
   Couette runs over shear rates and storage precisions.
 
@@ -105,36 +105,52 @@ def kolmogorov_run(lb, n: int = 128, U0: float = 0.1, steps: int = 2000, every: 
     return out
 
 
-def ageing_overlap(lb, n: int, seeds, t_w: int, taus, precision: str = "fp16", U0: float = 0.0,
+def ageing_overlap(lb, n: int, seeds, t_w, taus, precision: str = "fp16", U0: float = 0.0,
                    **kw):
     """C(t_w, tau) of Eq. (6): ensemble averages over `seeds` of
-    sum phi(t_w) phi(t_w + tau) / sum phi(t_w)^2, with the realisations
-    stepped together in one pool.  U0 > 0 adds the Kolmogorov forcing."""
+    sum phi(t_w) phi(t_w + tau) over the average of sum phi(t_w)^2, with
+    the realisations stepped together in one pool.  `t_w` is one waiting
+    time or a sequence of them (one pool run serves all); U0 > 0 adds the
+    Kolmogorov forcing.  Returns (taus, C), C of shape (len(taus),) for a
+    single t_w, else (len(t_w), len(taus))."""
     nu0 = CS2 * (kw.get("tau_A", 1.0) - 0.5)
     k = 2 * np.pi / n
     extra = dict(kolmo_amp=nu0 * k * k * U0, kolmo_k=1.0) if U0 else {}
     p = lb.make_params(n, n, precision, **kw, **extra)
-    taus = sorted(int(x) for x in taus)
-    total = t_w + taus[-1]
+    single = np.ndim(t_w) == 0
+    t_ws = [int(t_w)] if single else sorted(int(v) for v in t_w)
+    taus = sorted(int(v) for v in taus)
+    total = t_ws[-1] + taus[-1]
     budget = lb.Pool.footprint(p) * len(seeds) + (64 << 20)
-    num = np.zeros(len(taus))
-    den = 0.0
+    num = np.zeros((len(t_ws), len(taus)))
+    den = np.zeros(len(t_ws))
+    # every time at which the fields are read, with what to do there
+    events = {}
+    for a, w in enumerate(t_ws):
+        events.setdefault(w, []).append(("w", a, 0))
+        for b, tau in enumerate(taus):
+            events.setdefault(w + tau, []).append(("t", a, b))
     with lb.Pool(p, budget, max_jobs=len(seeds)) as pool:
         jobs = [pool.admit(p, int(s), total) for s in seeds]
-        pool.run(t_w)
-        phi_w = []
-        for j in jobs:
-            ra, rb, _, _ = pool.fields(j)
-            phi_w.append(ra - rb)
-            den += float((phi_w[-1] ** 2).sum())
-        t = t_w
-        for i, tau in enumerate(taus):
-            pool.run(t_w + tau - t)
-            t = t_w + tau
-            for j, pw in zip(jobs, phi_w):
+        phi_w = [[None] * len(jobs) for _ in t_ws]
+        t = 0
+        for when in sorted(events):
+            if when > t:
+                pool.run(when - t)
+                t = when
+            phis = []
+            for j in jobs:
                 ra, rb, _, _ = pool.fields(j)
-                num[i] += float((pw * (ra - rb)).sum())
-    return taus, num / den
+                phis.append(ra - rb)
+            # waiting-time snapshots first: tau = 0 reads the same fields
+            for kind, a, b in sorted(events[when], key=lambda e: e[0] != "w"):
+                if kind == "w":
+                    phi_w[a] = phis
+                    den[a] = sum(float((q * q).sum()) for q in phis)
+                else:
+                    num[a, b] = sum(float((q * r).sum()) for q, r in zip(phi_w[a], phis))
+    C = num / den[:, None]
+    return taus, (C[0] if single else C)
 
 
 def drop_fields(n: int, radius: float, rho_in, rho_out):
@@ -148,33 +164,54 @@ def drop_fields(n: int, radius: float, rho_in, rho_out):
     return ra, rb
 
 
-def laplace_test(lb, rho0: float, radii=(12, 16, 24), n: int = 96, steps: int = 20000,
-                 precision: str = "fp32", psi_form: int = 1, **kw):
-    """Equilibrate drops of A in B and fit p_in - p_out = sigma / R (2-D
-    Laplace law) with the bulk pressure of Eq. (3).  Returns (sigma, rows of
-    (R measured, dp))."""
-    c = dict(kw)
-    p = lb.make_params(n, n, precision, rho0=rho0, psi_form=psi_form, **c)
+def laplace_test(lb, rho0: float, radii=(12, 18, 26), n: int = 128, steps: int = 30000,
+                 avg_from: int = 20000, every: int = 1000, precision: str = "fp32",
+                 psi_form: int = 1, rho_dense: float = 1.12, rho_light: float = 0.07, **kw):
+    """Laplace test on drops of A in B: p_in - p_out = sigma / R in 2-D, with
+    the bulk pressure of Eq. (3) averaged over the drop interior
+    (r < R - 4) and the exterior (r > R + 6), and over the samples taken
+    every `every` steps from `avg_from` on.  The drop densities (rho_dense,
+    rho_light) are held fixed while rho0 varies: with Psi = sqrt(rho0)
+    (1 - exp(-rho/rho0)), drops whose densities scale with rho0 are exact
+    rescalings of one another, so sigma would only scale with rho0.
+    Returns dict(sigma, rows=[dict(R, dp, interior_cv)], uniform): sigma
+    from the least-squares fit dp = sigma / R, interior_cv the relative
+    spread of rho_A inside the drop (a drop whose dense phase breaks into
+    micro-domains has no single bulk pressure; uniform is False then)."""
+    p = lb.make_params(n, n, precision, rho0=rho0, psi_form=psi_form, **kw)
     Ga, Gr = (p.G_A1, p.G_B1), (p.G_A2, p.G_B2)
     pref = rho0 if psi_form == 1 else math.sqrt(rho0)
+    y, x = np.mgrid[0:n, 0:n]
+    rr = np.sqrt((x - n / 2 + 0.5) ** 2 + (y - n / 2 + 0.5) ** 2)
     rows = []
     for R in radii:
-        ra, rb = drop_fields(n, R, (1.6 * rho0, 0.1 * rho0), (0.1 * rho0, 1.6 * rho0))
+        ra, rb = drop_fields(n, R, (rho_dense, rho_light), (rho_light, rho_dense))
+        acc = []
         with lb.Lattice(p) as g:
             g.init_fields(ra, rb)
-            g.step(steps)
-            fa, fb, _, _ = g.fields()
-        pr = bulk_pressure(fa, fb, Ga, Gr, p.G_X, rho0, pref)
-        c0 = n // 2
-        p_in = float(pr[c0 - 2:c0 + 2, c0 - 2:c0 + 2].mean())
-        p_out = float(np.concatenate([pr[:3].ravel(), pr[-3:].ravel()]).mean())
-        phi = fa - fb
-        area = float((phi > 0).sum())
-        rows.append((math.sqrt(area / math.pi), p_in - p_out))
-    x = np.array([1.0 / r for r, _ in rows])
-    yv = np.array([d for _, d in rows])
-    sigma = float((x * yv).sum() / (x * x).sum())
-    return sigma, rows
+            g.step(avg_from)
+            t = avg_from
+            while True:
+                fa, fb, _, _ = g.fields()
+                Rm = math.sqrt(float((fa - fb > 0).sum()) / math.pi)
+                inner, outer = rr < Rm - 4, rr > Rm + 6
+                if inner.sum() < 4 or outer.sum() < 4:
+                    acc.append((Rm, float("nan"), float("inf")))
+                else:
+                    pr = bulk_pressure(fa, fb, Ga, Gr, p.G_X, rho0, pref)
+                    cv = float(fa[inner].std() / fa[inner].mean())
+                    acc.append((Rm, float(pr[inner].mean() - pr[outer].mean()), cv))
+                if t + every > steps:
+                    break
+                g.step(every)
+                t += every
+        a = np.array(acc)
+        rows.append(dict(R=float(a[:, 0].mean()), dp=float(a[:, 1].mean()),
+                         interior_cv=float(a[:, 2].max())))
+    xs = np.array([1.0 / r["R"] for r in rows])
+    ys = np.array([r["dp"] for r in rows])
+    sigma = float((xs * ys).sum() / (xs * xs).sum())
+    return dict(sigma=sigma, rows=rows, uniform=all(r["interior_cv"] < 0.05 for r in rows))
 
 
 def couette_study(lb, rates, precisions=("fp32", "fp16", "bf16"), n: int = 512,

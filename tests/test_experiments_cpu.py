@@ -78,3 +78,116 @@ def test_flat_interface_pressure_balance_oracle(O, caption):
     assert abs(p_a - p_b) < 2e-3 * abs(p_a)
     # spurious currents at the interface stay small (1e-6 here)
     assert np.abs(ux).max() < 1e-5 and np.abs(uy).max() < 1e-5
+
+
+class _OracleLb:
+    """The slice of the library's Python API that the experiment drivers
+    use (make_params, Lattice), run on the oracle so the drivers' host
+    logic is exercised on the CPU."""
+
+    def __init__(self, O, caption):
+        self.O, self.caption = O, caption
+
+    def make_params(self, nx, ny, precision="fp64", *, rho0=None, psi_form=0, **kw):
+        from types import SimpleNamespace
+        c = dict(self.caption)
+        if rho0 is not None:
+            c["rho0"] = rho0
+        P = self.O.make_params(nx, ny, psi_form=psi_form, **c, **kw)
+        return SimpleNamespace(P=P, G_A1=c["Ga"][0], G_B1=c["Ga"][1], G_A2=c["Gr"][0],
+                               G_B2=c["Gr"][1], G_X=c["GX"])
+
+    def Lattice(self, p):
+        O = self.O
+
+        class _L:
+            def __enter__(s):
+                s.t = 0
+                return s
+
+            def __exit__(s, *a):
+                return False
+
+            def init_fields(s, ra, rb):
+                s.f = O.init_fields(p.P, ra, rb)
+
+            def step(s, n):
+                assert O.run(p.P, s.f, n, t0=s.t) == 0
+                s.t += n
+
+            def fields(s):
+                return O.fields(p.P, s.f)
+
+        return _L()
+
+    @property
+    def Pool(self):
+        O = self.O
+
+        class _Pool:
+            @staticmethod
+            def footprint(p):
+                return 1
+
+            def __init__(s, p, budget, max_jobs):
+                s.jobs = []
+
+            def __enter__(s):
+                return s
+
+            def __exit__(s, *a):
+                return False
+
+            def admit(s, p, seed, steps):
+                s.jobs.append([p.P, O.init_seeded(p.P, seed), 0])
+                return len(s.jobs) - 1
+
+            def run(s, n):
+                for j in s.jobs:
+                    assert O.run(j[0], j[1], n, t0=j[2]) == 0
+                    j[2] += n
+                return len(s.jobs)
+
+            def fields(s, j):
+                return O.fields(s.jobs[j][0], s.jobs[j][1])
+
+        return _Pool
+
+
+def test_ageing_driver_on_oracle(O, caption):
+    """C(t_w, tau) from the pooled driver equals Eq. (6) evaluated on
+    separately run oracle realisations; C(t_w, 0) = 1."""
+    lb = _OracleLb(O, caption)
+    seeds, n = (0, 1, 2), 16
+    t_ws, taus = (20, 40), (0, 10, 30)
+    _, C = E.ageing_overlap(lb, n, seeds, t_ws, taus, precision="fp64", psi_form=1)
+    assert C.shape == (2, 3) and np.allclose(C[:, 0], 1.0, rtol=0, atol=1e-15)
+    P = lb.make_params(n, n, psi_form=1).P
+    phi = {}
+    for sd in seeds:
+        f = O.init_seeded(P, sd)
+        t = 0
+        for when in sorted({w + u for w in t_ws for u in taus}):
+            O.run(P, f, when - t, t0=t)
+            t = when
+            ra, rb, _, _ = O.fields(P, f)
+            phi[sd, when] = ra - rb
+    for a, w in enumerate(t_ws):
+        den = sum((phi[sd, w] ** 2).sum() for sd in seeds)
+        for b, u in enumerate(taus):
+            num = sum((phi[sd, w] * phi[sd, w + u]).sum() for sd in seeds)
+            assert abs(C[a, b] - num / den) < 1e-13
+    _, c1 = E.ageing_overlap(lb, n, seeds, 40, taus, precision="fp64", psi_form=1)
+    assert np.array_equal(c1, C[1])
+
+
+def test_laplace_driver_on_oracle(O, caption):
+    """The Laplace driver on oracle drops (psi_form = 1, rho0 = 0.55): the
+    pressure jump is positive, falls as 1/R within 20 %, and the dense
+    interior stays one uniform phase."""
+    out = E.laplace_test(_OracleLb(O, caption), 0.55, radii=(8, 12), n=48, steps=3000,
+                         avg_from=2000, every=500, precision="fp64", psi_form=1)
+    (r1, r2) = out["rows"]
+    assert out["uniform"] and out["sigma"] > 0
+    assert r1["dp"] > r2["dp"] > 0
+    assert abs(r1["dp"] * r1["R"] / (r2["dp"] * r2["R"]) - 1) < 0.2

@@ -334,6 +334,46 @@ def test_species_swap_symmetry(O, caption):
     assert np.array_equal(ux, vx) and np.array_equal(uy, vy)
 
 
+@pytest.mark.parametrize("psi_form", [0, 1])
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_density_scaling_invariance(O, caption, psi_form, scheme):
+    """Scaling all densities and rho0 by lam leaves the velocities unchanged
+    and scales every density by lam, provided the like-species couplings
+    scale as lam^(1 - 2a) with Psi = rho0^a (1 - exp(-rho/rho0)) (a = 1/2
+    for the form after Eq. (2), a = 1 for the other reading): then Psi^2 G
+    and (G^X/rho0) rho^2 both grow as lam, so F/rho and u_eq are unchanged
+    and f^eq grows as lam.  A dropped 1/rho0 in the G^X term, or a swapped
+    Psi prefactor, breaks this."""
+    n, lam = 20, 1.375
+    r0 = caption["rho0"]
+    a = 0.5 if psi_form == 0 else 1.0
+    g = lam ** (1 - 2 * a)
+    P = params(O, caption, n, n, psi_form=psi_form, force_scheme=scheme)
+    Q = params(O, caption, n, n, psi_form=psi_form, force_scheme=scheme, rho0=lam * r0,
+               Ga=tuple(g * v for v in caption["Ga"]), Gr=tuple(g * v for v in caption["Gr"]))
+    rng = np.random.default_rng(12)
+    rhoA = r0 * (1 + 0.03 * (2 * rng.random((n, n)) - 1))
+    rhoB = r0 * (1 + 0.03 * (2 * rng.random((n, n)) - 1))
+    f = O.init_fields(P, rhoA, rhoB)
+    h = O.init_fields(Q, lam * rhoA, lam * rhoB)
+    O.run(P, f, 40)
+    O.run(Q, h, 40)
+    ra, rb, ux, uy = O.fields(P, f)
+    sa, sb, vx, vy = O.fields(Q, h)
+    assert np.abs(ux).max() > 1e-4          # the dynamics is not trivial
+    assert np.abs(sa - lam * ra).max() < 1e-12 * lam * r0
+    assert np.abs(sb - lam * rb).max() < 1e-12 * lam * r0
+    assert np.abs(vx - ux).max() < 1e-12 and np.abs(vy - uy).max() < 1e-12
+    # without the coupling rescale (the reading where Psi carries rho0, and
+    # a = 1/2 needs none) the invariance is lost
+    if psi_form == 1:
+        R = params(O, caption, n, n, psi_form=1, force_scheme=scheme, rho0=lam * r0)
+        k = O.init_fields(R, lam * rhoA, lam * rhoB)
+        O.run(R, k, 40)
+        wa, _, _, _ = O.fields(R, k)
+        assert np.abs(wa - lam * ra).max() > 1e-4 * lam * r0
+
+
 # ----------------------------------------------------------- hydrodynamics
 @pytest.mark.parametrize("tau", [1.0, 0.8])
 def test_couette_profile_and_wall_stress(O, tau):
