@@ -17,7 +17,6 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // the D2Q9 weights w(|d|^2), for the 12 pair representatives used by the
 // kernels: (1,0) (0,1) (1,1) (-1,1) (2,0) (0,2) (2,1) (1,2) (-1,2) (-2,1)
 // (2,2) (-2,2).
-static const int kRepC2[12] = {1, 1, 2, 2, 4, 4, 5, 5, 5, 5, 8, 8};
 static double p_weight(int c2) {
     switch (c2) {
         case 1: return 4.0 / 63.0;
@@ -111,13 +110,22 @@ template <typename C>
 static void fill_coef(Coef<C>& k, const lb_params* p) {
     const double Ga[2] = {p->G_A1, p->G_B1};
     const double Gr[2] = {p->G_A2, p->G_B2};
-    for (int s = 0; s < 2; ++s)
-        for (int r = 0; r < 12; ++r) {
-            const int c2 = kRepC2[r];
-            const double v = (r < 4 ? Ga[s] * w_weight(c2) : 0.0) + Gr[s] * p_weight(c2);
-            k.K[s][r] = (C)v;
+    // d_x, d_y in {0, +-1, +-2}: the products below are exact
+    for (int r = 0; r < 12; ++r) {
+        const int c2 = rdx(r) * rdx(r) + rdy(r) * rdy(r);
+        C K[2];
+        for (int s = 0; s < 2; ++s)
+            K[s] = (C)((r < 4 ? Ga[s] * w_weight(c2) : 0.0) + Gr[s] * p_weight(c2));
+        k.KX[r].x = K[0] * (C)rdx(r);
+        k.KX[r].y = K[1] * (C)rdx(r);
+        k.KY[r].x = K[0] * (C)rdy(r);
+        k.KY[r].y = K[1] * (C)rdy(r);
+        if (r < 4) {
+            const C w = (C)w_weight(c2);
+            k.WX[r].x = k.WX[r].y = w * (C)rdx(r);
+            k.WY[r].x = k.WY[r].y = w * (C)rdy(r);
         }
-    for (int r = 0; r < 4; ++r) k.W[r] = (C)w_weight(kRepC2[r]);
+    }
     // Offsets are taken from rho_ref rounded to the compute precision, so that
     // rho = rho_ref + sum_i h_i holds with the same rho_ref on every path.
     const double rref = (double)(C)(p->rho_ref > 0.0 ? p->rho_ref : p->rho0);

@@ -45,11 +45,30 @@ struct Geom {
     int periodic;       // 1: periodic in y; 0: Couette walls in y
 };
 
-// Per-launch model coefficients, in the compute precision C.
+// One representative d of each +-d pair of the 24-neighbour stencil; the
+// first four are the first belt (also the pairs of the cross term).
+__host__ __device__ constexpr int rdx(int k) {
+    return k == 0 ? 1 : k == 1 ? 0 : k == 2 ? 1 : k == 3 ? -1 : k == 4 ? 2 : k == 5 ? 0
+         : k == 6 ? 2 : k == 7 ? 1 : k == 8 ? -1 : k == 9 ? -2 : k == 10 ? 2 : -2;
+}
+__host__ __device__ constexpr int rdy(int k) {
+    return k == 0 ? 0 : k == 1 ? 1 : k == 2 ? 1 : k == 3 ? 1 : k == 4 ? 0 : k == 5 ? 2
+         : k == 6 ? 1 : k == 7 ? 2 : k == 8 ? 2 : k == 9 ? 1 : k == 10 ? 2 : 2;
+}
+
+// The (A, B) pair type of a compute precision.
+template <typename C> struct PairOf;
+template <> struct PairOf<float> { typedef float2 T; };
+template <> struct PairOf<double> { typedef double2 T; };
+
+// Per-launch model coefficients, in the compute precision C.  Stencil
+// weights are (A, B) pairs already multiplied by the component of d, so that
+// one paired multiply-add serves both species.
 template <typename C>
 struct Coef {
-    C K[2][12];        // like-species pair weights G^a w(d) + G^r p(d), 12 reps d
-    C W[4];            // cross-species pair weights w(d), 4 reps d
+    typedef typename PairOf<C>::T C2;
+    C2 KX[12], KY[12]; // like-species weights (G^a w(d) + G^r p(d)) d_x, d_y per rep d
+    C2 WX[4], WY[4];   // cross-species weights w(d) d_x, w(d) d_y (same for A and B)
     C gx_rho0;         // G_X / rho0
     C psi_ref;         // Psi(rho_ref)
     C psi_scale;       // P exp(-rho_ref / rho0)

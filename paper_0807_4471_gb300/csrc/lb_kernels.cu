@@ -125,69 +125,61 @@ __device__ __forceinline__ void put2(T2* base, const Geom& g, int i, int x, int 
     }
 }
 
-template <typename C>
-__device__ __forceinline__ C sum9(const C h[9]) {
-    return ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
+// ((h0 + h1) + (h2 + h3)) + ((h4 + h5) + (h6 + h7)) + h8, per species.
+template <typename C2>
+__device__ __forceinline__ C2 sum9(const C2 h[9]) {
+    return padd(padd(padd(padd(h[0], h[1]), padd(h[2], h[3])), padd(padd(h[4], h[5]), padd(h[6], h[7]))),
+                h[8]);
 }
 
-// The offsets h_i(r, t) of both species at lattice row y.  bm, b0, bp point
-// at the site's pair in the staged rows y-1, y, y+1 of plane 0 (plane i is
-// PS pairs further).  pull = 1: streamed from h*(r - c_i, t - 1), with
-// halfway bounce-back at the Couette walls: f_i = f*_opp(i)(r)
-// + 6 w_i rho_w (c_i . u_w), rho_w the pre-streaming density of the
-// boundary node, rho_ref + sum_j h*_j(r).  pull = 0: the state in place.
+// The offsets h_i(r, t) of both species at lattice row y, as (A, B) pairs.
+// bm, b0, bp point at the site's pair in the staged rows y-1, y, y+1 of
+// plane 0 (plane i is PS pairs further).  pull = 1: streamed from
+// h*(r - c_i, t - 1), with halfway bounce-back at the Couette walls:
+// f_i = f*_opp(i)(r) + 6 w_i rho_w (c_i . u_w), rho_w the pre-streaming
+// density of the boundary node, rho_ref + sum_j h*_j(r).  pull = 0: the
+// state in place.
 template <int P, int PS>
 __device__ __forceinline__ void load_site(const typename Prec<P>::T2* bm,
                                           const typename Prec<P>::T2* b0,
                                           const typename Prec<P>::T2* bp, int y, bool per,
                                           int pull, const Geom& g,
                                           const LatVals<typename Prec<P>::C>& v,
-                                          typename Prec<P>::C hA[9], typename Prec<P>::C hB[9]) {
+                                          typename Prec<P>::C2 h[9]) {
     typedef typename Prec<P>::C C;
     typedef typename Prec<P>::C2 C2;
     if (pull) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const typename Prec<P>::T2* r = cy(i) == 1 ? bm : (cy(i) == -1 ? bp : b0);
-            const C2 q = dec2(r[i * PS - cx(i)]);
-            hA[i] = q.x;
-            hB[i] = q.y;
+            h[i] = dec2(r[i * PS - cx(i)]);
         }
         if (!per && (y == 0 || y == g.ny - 1)) {
-            C sA[9], sB[9];
+            C2 sv[9];
 #pragma unroll
-            for (int j = 0; j < 9; ++j) {
-                const C2 q = dec2(b0[j * PS]);
-                sA[j] = q.x;
-                sB[j] = q.y;
-            }
-            const C rwA = v.rho_ref + sum9(sA), rwB = v.rho_ref + sum9(sB);
+            for (int j = 0; j < 9; ++j) sv[j] = dec2(b0[j * PS]);
+            const C2 rw = padd(pset(v.rho_ref), sum9(sv));
             const int up = (y == 0);                 // links arriving upward
             const C uw = up ? -v.u_wall : v.u_wall;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 if ((up && cy(i) == 1) || (!up && cy(i) == -1)) {
                     const C m = C(6) * wgt<C>(i) * (C(cx(i)) * uw);
-                    hA[i] = sA[opp(i)] + m * rwA;
-                    hB[i] = sB[opp(i)] + m * rwB;
+                    h[i] = pfma(pset(m), rw, sv[opp(i)]);
                 }
             }
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const C2 q = dec2(b0[i * PS]);
-            hA[i] = q.x;
-            hB[i] = q.y;
-        }
+        for (int i = 0; i < 9; ++i) h[i] = dec2(b0[i * PS]);
     }
 }
 
-// Deviation of the pseudo-potential from Psi(rho_ref):
+// Deviation of the pseudo-potential from Psi(rho_ref), both species:
 // Psi(rho_ref + d) - Psi(rho_ref) = -P exp(-rho_ref/rho0) expm1(-d/rho0).
-template <typename C>
-__device__ __forceinline__ C dpsi_of(C d, const LatVals<C>& v) {
-    return -v.psi_scale * cexpm1(-d * v.inv_rho0);
+template <typename C, typename C2>
+__device__ __forceinline__ C2 dpsi_of(C2 d, const LatVals<C>& v) {
+    return pmul(pset(-v.psi_scale), pexpm1(pmul(d, pset(-v.inv_rho0))));
 }
 
 // Density and pseudo-potential deviations (rho - rho_ref, Psi - Psi(rho_ref))
@@ -198,41 +190,38 @@ __device__ __forceinline__ void cell_dev(const typename Prec<P>::T2* bm,
                                          const typename Prec<P>::T2* bp, int y, bool per, int pull,
                                          const Geom& g, const LatVals<typename Prec<P>::C>& v,
                                          typename Prec<P>::C2& r, typename Prec<P>::C2& q) {
-    typedef typename Prec<P>::C C;
-    C hA[9], hB[9];
-    load_site<P, PS>(bm, b0, bp, y, per, pull, g, v, hA, hB);
-    r.x = sum9(hA);
-    r.y = sum9(hB);
-    q.x = dpsi_of(r.x, v);
-    q.y = dpsi_of(r.y, v);
+    typename Prec<P>::C2 h[9];
+    load_site<P, PS>(bm, b0, bp, y, per, pull, g, v, h);
+    r = sum9(h);
+    q = dpsi_of(r, v);
 }
 
-// Post-collision offsets of one species (Eq. (1), BGK toward the
-// equilibrium at velocity (ux, uy)):
+// Post-collision offsets of both species (Eq. (1), BGK toward the
+// equilibrium at velocity (ux, uy), per species):
 // h*_i = h_i + omega (heq_i - h_i) [+ 3 w_i c_i . F for the source scheme],
 // heq_i = f^eq_i - w_i rho_ref = w_i [d_rho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u^2)],
 // evaluated per pair (i, opp(i)), whose c.u differ only in sign:
 // heq = E +- O with E = w (d_rho - 1.5 rho u^2 + 4.5 rho (c.u)^2), O = 3 w rho c.u.
-template <typename C, bool SRC>
-__device__ __forceinline__ void collide(const C h[9], C out[9], C drho, C rho, C ux, C uy,
-                                        C om, C Fx, C Fy) {
-    const C Q = drho - rho * (C(1.5) * (ux * ux + uy * uy));
-    out[0] = h[0] + om * (wgt<C>(0) * Q - h[0]);
+template <typename C, typename C2, bool SRC>
+__device__ __forceinline__ void collide(const C2 h[9], C2 out[9], C2 drho, C2 rho, C2 ux, C2 uy,
+                                        C2 om, C2 Fx, C2 Fy) {
+    const C2 Q = pfma(pmul(rho, pset(C(-1.5))), pfma(ux, ux, pmul(uy, uy)), drho);
+    out[0] = pfma(om, psub(pmul(pset(wgt<C>(0)), Q), h[0]), h[0]);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int i = k == 0 ? 1 : (k == 1 ? 2 : (k == 2 ? 5 : 6));   // c.u = ux, uy, ux+uy, uy-ux
         const int j = opp(i);
-        const C cu = C(cx(i)) * ux + C(cy(i)) * uy;
+        const C2 cu = k == 0 ? ux : (k == 1 ? uy : (k == 2 ? padd(ux, uy) : psub(uy, ux)));
         const C w = wgt<C>(i);
-        const C rcu = rho * cu;
-        const C E = w * (Q + C(4.5) * cu * rcu);
-        const C O = (C(3) * w) * rcu;
-        out[i] = h[i] + om * ((E + O) - h[i]);
-        out[j] = h[j] + om * ((E - O) - h[j]);
+        const C2 rcu = pmul(rho, cu);
+        const C2 E = pmul(pset(w), pfma(pmul(pset(C(4.5)), cu), rcu, Q));
+        const C2 O = pmul(pset(C(3) * w), rcu);
+        out[i] = pfma(om, psub(padd(E, O), h[i]), h[i]);
+        out[j] = pfma(om, psub(psub(E, O), h[j]), h[j]);
         if (SRC) {
-            const C S = (C(3) * w) * (C(cx(i)) * Fx + C(cy(i)) * Fy);
-            out[i] += S;
-            out[j] -= S;
+            const C2 S = pmul(pset(C(3) * w), pfma(pset(C(cx(i))), Fx, pmul(pset(C(cy(i))), Fy)));
+            out[i] = padd(out[i], S);
+            out[j] = psub(out[j], S);
         }
     }
 }
@@ -242,6 +231,7 @@ template <typename T2>
 struct SiteOut {
     T2* stage;             // staging tile slot of the site (full tiles), or null
     T2* fout;              // output buffer (ragged tiles and ghost copies)
+    bool edge;             // the tile may hold sites with periodic ghost copies
     int obs;               // ObsKind (observe kernel) or OBS_NONE
     double* obs_out;
     int q0, q1;
@@ -250,8 +240,9 @@ struct SiteOut {
 // One lattice site: moments, the force of Eq. (2) from the staged deviation
 // rows, and either the forced BGK collision and write-back (OBS = false) or
 // the observables (OBS = true).  ps[k] / rr[k]: Psi / rho deviation rows
-// y + k - 2, pointing at the site's column.  red accumulates the bottom/top
-// wall momentum (step) or mass_A, mass_B, mom_x, mom_y (observe).
+// y + k - 2, pointing at the site's column; rr[2][0] holds the site's own
+// density deviations, summed from the same populations.  Both species are
+// carried as (A, B) pairs throughout.
 template <int P, bool OBS, bool GEN, int PS>
 __device__ __forceinline__ void site_update(
     const typename Prec<P>::T2* bm, const typename Prec<P>::T2* b0,
@@ -262,81 +253,58 @@ __device__ __forceinline__ void site_update(
     typedef typename Prec<P>::T2 T2;
     typedef typename Prec<P>::C C;
     typedef typename Prec<P>::C2 C2;
-    C h[2][9];
-    load_site<P, PS>(bm, b0, bp, y, per, pull, g, v, h[0], h[1]);
-    C drho[2], rho[2], jx[2], jy[2];
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        drho[s] = sum9(h[s]);
-        rho[s] = v.rho_ref + drho[s];
-        // sum_i w_i c_i = 0, so the offsets carry all of j
-        const C d57 = h[s][5] - h[s][7], d68 = h[s][6] - h[s][8];
-        jx[s] = (h[s][1] - h[s][3]) + (d57 - d68);
-        jy[s] = (h[s][2] - h[s][4]) + (d57 + d68);
-    }
-    if (!(isfinite(rho[0]) && isfinite(rho[1]))) bad = true;
+    C2 h[9];
+    load_site<P, PS>(bm, b0, bp, y, per, pull, g, v, h);
+    const C2 drho = rr[2][0];
+    const C2 rho = padd(pset(v.rho_ref), drho);
+    // sum_i w_i c_i = 0, so the offsets carry all of j
+    const C2 d57 = psub(h[5], h[7]), d68 = psub(h[6], h[8]);
+    const C2 jx = padd(psub(h[1], h[3]), psub(d57, d68));
+    const C2 jy = padd(psub(h[2], h[4]), padd(d57, d68));
+    if (!(isfinite(rho.x) && isfinite(rho.y))) bad = true;
 
     // Eq. (2): F_s = -Psi_s(r) sum_d K_s(d) d [Psi_s(r+d) - Psi_s(r-d)]
     //               - (G_X/rho0) rho_s(r) sum_d w(d) d [rho_s'(r+d) - rho_s'(r-d)]
     // over one representative d of each +-d pair (the reference values cancel
     // in the differences); belt-1 and belt-2 pairs accumulate separately.
-    C axA1 = C(0), ayA1 = C(0), axB1 = C(0), ayB1 = C(0);
-    C axA2 = C(0), ayA2 = C(0), axB2 = C(0), ayB2 = C(0);
+    C2 ax1 = pset(C(0)), ay1 = pset(C(0)), ax2 = pset(C(0)), ay2 = pset(C(0));
 #pragma unroll
     for (int q = 0; q < 12; ++q) {
         const int dx = rdx(q), dy = rdy(q);
-        const C2 pp = ps[2 + dy][dx], pm = ps[2 - dy][-dx];
-        const C dA = pp.x - pm.x, dB = pp.y - pm.y;
-        C& axA = q < 4 ? axA1 : axA2;
-        C& ayA = q < 4 ? ayA1 : ayA2;
-        C& axB = q < 4 ? axB1 : axB2;
-        C& ayB = q < 4 ? ayB1 : ayB2;
-        if (dx != 0) {
-            axA += (k.K[0][q] * C(dx)) * dA;
-            axB += (k.K[1][q] * C(dx)) * dB;
-        }
-        if (dy != 0) {
-            ayA += (k.K[0][q] * C(dy)) * dA;
-            ayB += (k.K[1][q] * C(dy)) * dB;
-        }
+        const C2 dp = psub(ps[2 + dy][dx], ps[2 - dy][-dx]);
+        C2& ax = q < 4 ? ax1 : ax2;
+        C2& ay = q < 4 ? ay1 : ay2;
+        if (dx != 0) ax = pfma(k.KX[q], dp, ax);
+        if (dy != 0) ay = pfma(k.KY[q], dp, ay);
     }
-    C qxA = C(0), qyA = C(0), qxB = C(0), qyB = C(0);
+    // cross term: (sum w d_x [rho_A(r+d) - rho_A(r-d)], same for B); species
+    // A feels rho_B, so the pair is used swapped
+    C2 qx = pset(C(0)), qy = pset(C(0));
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int dx = rdx(q), dy = rdy(q);
-        const C2 rp = rr[2 + dy][dx], rm = rr[2 - dy][-dx];
-        const C dB = rp.y - rm.y, dA = rp.x - rm.x;   // A feels rho_B, B feels rho_A
-        if (dx != 0) {
-            qxA += (k.W[q] * C(dx)) * dB;
-            qxB += (k.W[q] * C(dx)) * dA;
-        }
-        if (dy != 0) {
-            qyA += (k.W[q] * C(dy)) * dB;
-            qyB += (k.W[q] * C(dy)) * dA;
-        }
+        const C2 dr = psub(rr[2 + dy][dx], rr[2 - dy][-dx]);
+        if (dx != 0) qx = pfma(k.WX[q], dr, qx);
+        if (dy != 0) qy = pfma(k.WY[q], dr, qy);
     }
-    const C2 pc = ps[2][0];
-    const C pcA = v.psi_ref + pc.x, pcB = v.psi_ref + pc.y;
-    C Fx[2], Fy[2];
-    Fx[0] = -pcA * (axA1 + axA2) - v.gx_rho0 * rho[0] * qxA;
-    Fy[0] = -pcA * (ayA1 + ayA2) - v.gx_rho0 * rho[0] * qyA;
-    Fx[1] = -pcB * (axB1 + axB2) - v.gx_rho0 * rho[1] * qxB;
-    Fy[1] = -pcB * (ayB1 + ayB2) - v.gx_rho0 * rho[1] * qyB;
+    const C2 npc = psub(pset(-v.psi_ref), ps[2][0]);      // -Psi_s(r)
+    const C2 ng = pmul(pset(-v.gx_rho0), rho);             // -(G_X/rho0) rho_s
+    C2 Fx = pfma(npc, padd(ax1, ax2), pmul(ng, pair(qx.y, qx.x)));
+    C2 Fy = pfma(npc, padd(ay1, ay2), pmul(ng, pair(qy.y, qy.x)));
     if (GEN && k.has_accel) {
         C acc = k.g_x;
         if (k.kolmo_amp != C(0)) acc += k.kolmo_amp * csin(k.kolmo_w * C(y));
-        Fx[0] += rho[0] * acc;
-        Fx[1] += rho[1] * acc;
+        Fx = pfma(rho, pset(acc), Fx);
     }
 
     if (OBS) {
         const long long N = (long long)g.nx * g.ny;
         const long long idx = (long long)y * g.nx + x;
-        const double rA = (double)v.rho_ref + (double)drho[0];
-        const double rB = (double)v.rho_ref + (double)drho[1];
+        const double rA = (double)v.rho_ref + (double)drho.x;
+        const double rB = (double)v.rho_ref + (double)drho.y;
         const double tot = rA + rB;
-        const double mx = (double)jx[0] + (double)jx[1] + 0.5 * ((double)Fx[0] + (double)Fx[1]);
-        const double my = (double)jy[0] + (double)jy[1] + 0.5 * ((double)Fy[0] + (double)Fy[1]);
+        const double mx = (double)jx.x + (double)jx.y + 0.5 * ((double)Fx.x + (double)Fx.y);
+        const double my = (double)jy.x + (double)jy.y + 0.5 * ((double)Fy.x + (double)Fy.y);
         if (o.obs == OBS_FIELDS) {
             o.obs_out[idx] = rA;
             o.obs_out[N + idx] = rB;
@@ -347,7 +315,8 @@ __device__ __forceinline__ void site_update(
             for (int q = 0; q < 18; ++q)
                 if (q >= o.q0 && q < o.q1)
                     o.obs_out[(long long)(q - o.q0) * N + idx] =
-                        (double)h[q / 9][q % 9] + wgt<double>(q % 9) * (double)v.rho_ref;
+                        (double)(q < 9 ? h[q % 9].x : h[q % 9].y) +
+                        wgt<double>(q % 9) * (double)v.rho_ref;
         }
         red[0] += rA;
         red[1] += rB;
@@ -358,42 +327,40 @@ __device__ __forceinline__ void site_update(
 
     // Eq. (1): forced BGK relaxation.  Common velocity
     // u' = sum_s (j_s/tau_s) / sum_s (rho_s/tau_s); shift u_s = u' + tau_s F_s/rho_s.
-    const C den = rho[0] * k.omega[0] + rho[1] * k.omega[1];
-    C upx = C(0), upy = C(0);
-    if (den != C(0)) {
-        const C inv = recip(den);
-        upx = (jx[0] * k.omega[0] + jx[1] * k.omega[1]) * inv;
-        upy = (jy[0] * k.omega[0] + jy[1] * k.omega[1]) * inv;
-    }
+    // (selects, not branches: an empty site has u' = 0 and no shift)
+    const C2 om = pair(k.omega[0], k.omega[1]);
+    const C2 ro = pmul(rho, om), jxo = pmul(jx, om), jyo = pmul(jy, om);
+    const C den = ro.x + ro.y;
+    const C inv = den != C(0) ? recip(den) : C(0);
+    const C2 up = pair((jxo.x + jxo.y) * inv, (jyo.x + jyo.y) * inv);
     const bool source = GEN && k.source;
-    C hs[2][9];
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        C ux = upx, uy = upy;
-        if (!source && rho[s] != C(0)) {
-            const C tr = k.tau[s] * recip(rho[s]);
-            ux += tr * Fx[s];
-            uy += tr * Fy[s];
-        }
-        if (source)
-            collide<C, true>(h[s], hs[s], drho[s], rho[s], ux, uy, k.omega[s], Fx[s], Fy[s]);
-        else
-            collide<C, false>(h[s], hs[s], drho[s], rho[s], ux, uy, k.omega[s], Fx[s], Fy[s]);
+    C2 ux = pset(up.x), uy = pset(up.y);
+    if (!source) {
+        const C2 tr = pair(rho.x != C(0) ? k.tau[0] * recip(rho.x) : C(0),
+                           rho.y != C(0) ? k.tau[1] * recip(rho.y) : C(0));
+        ux = pfma(tr, Fx, ux);
+        uy = pfma(tr, Fy, uy);
     }
+    C2 hs[9];
+    if (source)
+        collide<C, C2, true>(h, hs, drho, rho, ux, uy, om, Fx, Fy);
+    else
+        collide<C, C2, false>(h, hs, drho, rho, ux, uy, om, Fx, Fy);
     T2 e[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) e[i] = enc2<T2, C>(hs[0][i], hs[1][i]);
+    for (int i = 0; i < 9; ++i) e[i] = enc2<T2, C>(hs[i].x, hs[i].y);
 
     // Full tiles go through the staging tile and a bulk tensor store; ragged
     // tiles and periodic ghost copies use plain stores.
     constexpr int TX = Prec<P>::TX, TY = Prec<P>::TY;
-    const int dX = (x < 3) ? g.nx : ((x >= g.nx - 3) ? -g.nx : 0);
-    long long dY = 0;
-    if (per) dY = (y < 3) ? (long long)g.ny * g.pitch : ((y >= g.ny - 3) ? -(long long)g.ny * g.pitch : 0);
     if (o.stage != nullptr) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) o.stage[i * TY * TX] = e[i];
     }
+    const int dX = !o.edge ? 0 : (x < 3) ? g.nx : ((x >= g.nx - 3) ? -g.nx : 0);
+    long long dY = 0;
+    if (per && o.edge)
+        dY = (y < 3) ? (long long)g.ny * g.pitch : ((y >= g.ny - 3) ? -(long long)g.ny * g.pitch : 0);
     if (o.stage == nullptr || dX != 0 || dY != 0) {
         const long long PL = (long long)g.rows * g.pitch;
         T2* __restrict__ out = o.fout + (long long)(y + kGY) * g.pitch + (x + g.gx);
@@ -414,20 +381,17 @@ __device__ __forceinline__ void site_update(
         // rho_w (c_i . u_w), from the stored (rounded) values.
         const int down = (y == 0);
         const C uw = down ? -v.u_wall : v.u_wall;
-        C sA[9], sB[9];
+        C2 sv[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const C2 q = dec2(e[i]);
-            sA[i] = q.x;
-            sB[i] = q.y;
-        }
-        const C rw[2] = {v.rho_ref + sum9(sA), v.rho_ref + sum9(sB)};
+        for (int i = 0; i < 9; ++i) sv[i] = dec2(e[i]);
+        const C2 rw2 = padd(pset(v.rho_ref), sum9(sv));
+        const C rw[2] = {rw2.x, rw2.y};
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             if ((down && cy(i) == -1) || (!down && cy(i) == 1)) {
 #pragma unroll
                 for (int s = 0; s < 2; ++s) {
-                    const C fi = (s ? sB[i] : sA[i]) + wgt<C>(i) * v.rho_ref;
+                    const C fi = (s ? sv[i].y : sv[i].x) + wgt<C>(i) * v.rho_ref;
                     const C back = fi - C(6) * wgt<C>(i) * rw[s] * (C(cx(i)) * uw);
                     const double dp = (double)(C(cx(i)) * (fi + back));
                     if (down) red[0] += dp; else red[1] += dp;
@@ -465,10 +429,13 @@ __device__ __forceinline__ void block_sum4(double red[4], double (*s_red)[4]) {
 // of rows and halo columns are shared through L2).  CTA b takes items
 // b, b + gridDim.x, ...  Walking down a strip, a CTA keeps the 8-row blocks
 // of f* (TMA-loaded into a ring of NB slots, one block ahead of use and
-// across item boundaries) and the density/Psi deviation rows (a ring of 16
-// rows), so each block is loaded and each deviation row computed once per
-// strip; only the x halo (4 of 72 columns) is redundant.  Full tiles are
-// written back by TMA bulk tensor stores.  The last CTA to finish advances
+// across item boundaries) and a window of the density/Psi deviation rows
+// y0 - 2 .. y0 + 9 of the current tile, whose last four rows are carried
+// forward as the next tile's first four; so each block is loaded and each
+// deviation row computed once per strip, and only the x halo (4 of 64
+// columns) is redundant.  Every thread keeps one column and row of the
+// window in both phases, so all its shared-memory addresses are fixed.
+// Full tiles are written back by TMA bulk tensor stores.  The last CTA to finish advances
 // every lattice's step counter and buffer parity and takes the Couette wall
 // samples.
 // V: bit 0 = every lattice periodic (no wall code); bit 1 = general forcing.
@@ -486,8 +453,8 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
     // 128-byte aligned base, derived from the shared array by indexing so
     // that every access below compiles to shared-memory instructions.
     unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    C2* ring_r = reinterpret_cast<C2*>(smem + L::RING_OFF);   // [RING][RX]
-    C2* ring_p = ring_r + L::RING * L::RX;                    // [RING][RX]
+    C2* win_r = reinterpret_cast<C2*>(smem + L::WIN_OFF);     // [WIN][RX]
+    C2* win_p = win_r + L::WIN * L::RX;                       // [WIN][RX]
     T2* stage = reinterpret_cast<T2*>(smem + L::STAGE_OFF);   // [9][TY][TX]
     __shared__ __align__(8) uint64_t bars[L::NB];
     __shared__ int s_fail, s_last;
@@ -495,6 +462,9 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
 
     const int tid = threadIdx.x;
     const int G = gridDim.x;
+    // window column and tile row of this thread (both phases)
+    const int t_lx = tid % L::RX, t_j = tid / L::RX;
+    static_assert(L::NT == L::RX * L::TY && L::TY >= 4, "one window cell per thread and row");
     auto slot = [&](int pos) { return reinterpret_cast<T2*>(smem + (pos % L::NB) * L::SLOT_BYTES); };
     // descriptor of the lattice that owns work item it (descriptors sorted by item0)
     auto find = [&](int it) {
@@ -562,7 +532,6 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
         const int cur = *((volatile int*)&d->st->cur);
         const int pull = *((volatile int*)&d->st->pull);
         T2* fout = reinterpret_cast<T2*>(d->fbuf[cur ^ 1]);
-        auto rrow = [&](C2* ring, int y) { return ring + ((y + L::RING) & (L::RING - 1)) * L::RX; };
         double wall[2] = {0.0, 0.0};
         for (int ty = ty_a; ty < ty_b; ++ty) {
             const int q = c_pos + (ty - ty_a);   // this tile uses blocks q and q + 1
@@ -573,67 +542,91 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
                 s_fail = 1;
             const int y0 = ty * L::TY;
             // The tile's padded rows [8 ty, 8 ty + 16) are blocks q (slot s0) and
-            // q + 1 (slot s1); row pointers address plane 0.
+            // q + 1 (slot s1); brow(r, c): row 8 ty + r, pair column c, plane 0.
             const T2* s0 = slot(q);
             const T2* s1 = slot(q + 1);
-            auto brow = [&](int R, int c) {
-                const int r = R - L::TYB * ty;
+            auto brow = [&](int r, int c) {
                 return (r < L::TYB ? s0 + r * L::BX : s1 + (r - L::TYB) * L::BX) + c;
             };
 
-            // Phase 2: deviation rows new to this tile (all 12 at an item's start).
-            const int r_lo = (ty == ty_a) ? y0 - 2 : y0 + 2;
-            const int ncell = (y0 + L::TY + 2 - r_lo) * L::RX;
-            for (int c = tid; c < ncell; c += L::NT) {
-                const int ly = c / L::RX, lx = c - ly * L::RX;
-                const int y = r_lo + ly;
-                if (!per && (y < 0 || y >= g.ny)) continue;
-                const int bc = lx - 2 + L::GX;   // pair column in the block
-                const int R = y + kGY;
-                C2 r, p;
-                cell_dev<P, PS>(brow(R - 1, bc), brow(R, bc), brow(R + 1, bc), y, per, pull, g, v,
-                                r, p);
-                rrow(ring_r, y)[lx] = r;
-                rrow(ring_p, y)[lx] = p;
+            // Phase 2: window row k holds lattice row y0 - 2 + k (padded row
+            // 8 ty + 1 + k).  Rows 4 .. TY + 3 are new: thread row t_j computes
+            // row 4 + t_j.  Rows 0 .. 3 are the previous tile's rows TY .. TY + 3,
+            // carried forward by the threads that own those (t_j >= TY - 4)
+            // before they overwrite them, or at an item's first tile computed
+            // from block q.  No other thread touches these cells in this phase.
+            {
+                const int bc = t_lx - 2 + L::GX;   // pair column in the block
+                if (t_j >= L::TY - 4) {
+                    const int k = t_j - (L::TY - 4);
+                    if (ty == ty_a) {
+                        const int y = y0 - 2 + k;
+                        if (per || (y >= 0 && y < g.ny)) {
+                            C2 r, p;
+                            cell_dev<P, PS>(brow(k, bc), brow(k + 1, bc), brow(k + 2, bc), y, per,
+                                            pull, g, v, r, p);
+                            win_r[k * L::RX + t_lx] = r;
+                            win_p[k * L::RX + t_lx] = p;
+                        }
+                    } else {
+                        win_r[k * L::RX + t_lx] = win_r[(L::TY + k) * L::RX + t_lx];
+                        win_p[k * L::RX + t_lx] = win_p[(L::TY + k) * L::RX + t_lx];
+                    }
+                }
+                const int k = 4 + t_j;
+                const int y = y0 + 2 + t_j;
+                if (per || y < g.ny) {
+                    C2 r, p;
+                    cell_dev<P, PS>(brow(k, bc), brow(k + 1, bc), brow(k + 2, bc), y, per, pull, g,
+                                    v, r, p);
+                    win_r[k * L::RX + t_lx] = r;
+                    win_p[k * L::RX + t_lx] = p;
+                }
             }
             if (!per) {   // mirror the deviations about the halfway walls
                 __syncthreads();
-                for (int c = tid; c < ncell; c += L::NT) {
-                    const int ly = c / L::RX, lx = c - ly * L::RX;
-                    const int y = r_lo + ly;
+                for (int c = tid; c < L::WIN * L::RX; c += L::NT) {
+                    const int k = c / L::RX, lx = c - k * L::RX;
+                    const int y = y0 - 2 + k;
                     int ym;
                     if (y < 0) ym = -1 - y;
                     else if (y >= g.ny && y <= g.ny + 1) ym = 2 * g.ny - 1 - y;
                     else continue;
-                    rrow(ring_r, y)[lx] = rrow(ring_r, ym)[lx];
-                    rrow(ring_p, y)[lx] = rrow(ring_p, ym)[lx];
+                    const int km = ym - (y0 - 2);   // in [0, WIN): see the wall cases
+                    win_r[k * L::RX + lx] = win_r[km * L::RX + lx];
+                    win_p[k * L::RX + lx] = win_p[km * L::RX + lx];
                 }
             }
             if (tid == 0) bulk_wait_read();   // previous bulk store has read the staging tile
             __syncthreads();
             if (s_fail) break;
 
-            // Phase 3: one site per thread (lx < TX).
+            // Phase 3: one site per thread (lx < TX): site (x0 + t_lx, y0 + t_j),
+            // whose rows y - 2 .. y + 2 are window rows t_j .. t_j + 4 and whose
+            // populations sit in padded rows 8 ty + 2 + t_j .. 8 ty + 4 + t_j.
             const bool full = x0 + L::TX <= g.nx && y0 + L::TY <= g.ny;
+            // only tiles within 3 sites of an edge write periodic ghost copies
+            const bool edge = !full || x0 < 3 || x0 + L::TX > g.nx - 3 ||
+                              (per && (y0 < 3 || y0 + L::TY > g.ny - 3));
             {
-                const int lx = tid % L::RX, ly = tid / L::RX;
+                const int lx = t_lx, ly = t_j;
                 const int x = x0 + lx, y = y0 + ly;
                 if (lx < L::TX && x < g.nx && y < g.ny) {
                     const int bc = lx + L::GX;
-                    const int R = y + kGY;
                     const C2* ps[5];
                     const C2* rr[5];
 #pragma unroll
                     for (int k2 = 0; k2 < 5; ++k2) {
-                        ps[k2] = rrow(ring_p, y + k2 - 2) + lx + 2;
-                        rr[k2] = rrow(ring_r, y + k2 - 2) + lx + 2;
+                        ps[k2] = win_p + (ly + k2) * L::RX + lx + 2;
+                        rr[k2] = win_r + (ly + k2) * L::RX + lx + 2;
                     }
                     SiteOut<T2> o;
                     o.stage = full ? stage + ly * L::TX + lx : nullptr;
                     o.fout = fout;
+                    o.edge = edge;
                     o.obs = OBS_NONE;
                     double wr[4] = {0.0, 0.0, 0.0, 0.0};
-                    site_update<P, false, GEN, PS>(brow(R - 1, bc), brow(R, bc), brow(R + 1, bc),
+                    site_update<P, false, GEN, PS>(brow(ly + 2, bc), brow(ly + 3, bc), brow(ly + 4, bc),
                                                    ps, rr, x, y, per, pull, g, v, a.k, o, wr, bad);
                     wall[0] += wr[0];
                     wall[1] += wr[1];
@@ -799,6 +792,7 @@ __global__ void __launch_bounds__(Layout<P>::NT)
             SiteOut<T2> o;
             o.stage = nullptr;
             o.fout = nullptr;
+            o.edge = false;
             o.obs = a.obs;
             o.obs_out = a.obs_out;
             o.q0 = a.q0;

@@ -25,17 +25,6 @@ template <typename C>
 __device__ __forceinline__ C wgt(int i) {
     return i == 0 ? C(4) / C(9) : (i <= 4 ? C(1) / C(9) : C(1) / C(36));
 }
-// One representative d of each +-d pair of the 24-neighbour stencil; the
-// first four are the first belt (also the pairs of the cross term).
-__host__ __device__ constexpr int rdx(int k) {
-    return k == 0 ? 1 : k == 1 ? 0 : k == 2 ? 1 : k == 3 ? -1 : k == 4 ? 2 : k == 5 ? 0
-         : k == 6 ? 2 : k == 7 ? 1 : k == 8 ? -1 : k == 9 ? -2 : k == 10 ? 2 : -2;
-}
-__host__ __device__ constexpr int rdy(int k) {
-    return k == 0 ? 0 : k == 1 ? 1 : k == 2 ? 1 : k == 3 ? 1 : k == 4 ? 0 : k == 5 ? 2
-         : k == 6 ? 1 : k == 7 ? 2 : k == 8 ? 2 : k == 9 ? 1 : k == 10 ? 2 : 2;
-}
-
 // ------------------------------------------------------- storage formats
 // In HBM and in shared memory the two species of one direction are stored
 // as an interleaved pair (A, B), so that one vector access serves both.
@@ -96,12 +85,66 @@ template <> __device__ __forceinline__ __nv_bfloat162 encd2<__nv_bfloat162>(doub
     return __halves2bfloat162(__double2bfloat16(a), __double2bfloat16(b));
 }
 
-// Correctly rounded reciprocal (no division slow path in FP32).
-__device__ __forceinline__ double recip(double v) { return 1.0 / v; }
-__device__ __forceinline__ float recip(float v) { return __frcp_rn(v); }
+// Arithmetic on the (A, B) pair of a site.  FP32: the packed two-lane
+// instructions of sm_100 and later (one instruction for both species, each
+// lane rounded to nearest like the scalar operation); FP64: two scalar ones.
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<const unsigned long long*>(&a)),
+          "l"(*reinterpret_cast<const unsigned long long*>(&b)));
+    return *reinterpret_cast<const float2*>(&d);
+}
+__device__ __forceinline__ double2 padd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 psub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 pmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 pset(float v) { return make_float2(v, v); }
+__device__ __forceinline__ double2 pset(double v) { return make_double2(v, v); }
+__device__ __forceinline__ float2 pair(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 pair(double a, double b) { return make_double2(a, b); }
 
-__device__ __forceinline__ double cexpm1(double v) { return expm1(v); }
-__device__ __forceinline__ float cexpm1(float v) { return expm1f(v); }
+// Reciprocal: correctly rounded in FP64; in FP32 the hardware approximation
+// (rcp.approx.ftz, within 1 ulp), which has no slow path or branch.
+__device__ __forceinline__ double recip(double v) { return 1.0 / v; }
+__device__ __forceinline__ float recip(float v) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+// exp(x) - 1 of a pair.  FP64: the library function.  FP32: branch-free, by the
+// Cody-Waite reduction x = k ln2 + r (|r| <= ln2 / 2, ln2 split into a
+// 16-bit head and a tail so that k * head is exact) and
+// expm1(x) = 2^k expm1(r) + (2^k - 1), with expm1(r) from its Taylor series
+// through r^7 / 7! (truncation below 1.6e-8 relative on |r| <= ln2 / 2).
+// Relative error about 2 ulp; a NaN argument gives NaN.  2^k is assembled
+// in the exponent field, k clamped to the normal range.
+__device__ __forceinline__ double2 pexpm1(double2 v) { return make_double2(expm1(v.x), expm1(v.y)); }
+__device__ __forceinline__ float2 pexpm1(float2 x) {
+    const float2 kr = pmul(x, pset(1.44269504088896341f));
+    const float2 k = make_float2(fminf(fmaxf(rintf(kr.x), -126.0f), 127.0f),
+                                 fminf(fmaxf(rintf(kr.y), -126.0f), 127.0f));
+    float2 r = pfma(k, pset(-0.693145751953125f), x);
+    r = pfma(k, pset(-1.42860676533018700e-06f), r);
+    float2 t = pset(1.0f / 5040.0f);
+    t = pfma(t, r, pset(1.0f / 720.0f));
+    t = pfma(t, r, pset(1.0f / 120.0f));
+    t = pfma(t, r, pset(1.0f / 24.0f));
+    t = pfma(t, r, pset(1.0f / 6.0f));
+    t = pfma(t, r, pset(0.5f));
+    t = pfma(t, r, pset(1.0f));
+    const float2 p = pmul(t, r);
+    const float2 s = make_float2(__int_as_float(((int)k.x + 127) << 23),
+                                 __int_as_float(((int)k.y + 127) << 23));
+    return pfma(s, p, padd(s, pset(-1.0f)));
+}
 __device__ __forceinline__ double csin(double v) { return sin(v); }
 __device__ __forceinline__ float csin(float v) { return sinf(v); }
 
@@ -121,12 +164,13 @@ struct Layout {
     static constexpr int NT = RX * TY;
     static constexpr int TYB = 8;                     // rows of a step-kernel block
     static constexpr int NB = Prec<P>::NB;            // ring slots of blocks
-    static constexpr int RING = 16;                   // rho/Psi ring rows (>= TY + 4 + TY/2)
-    // step kernel: NB block slots, the rho and Psi rings, the staging tile
+    // rho/Psi deviation window of a tile: rows y0 - 2 .. y0 + TY + 1
+    static constexpr int WIN = TY + 4;
+    // step kernel: NB block slots, the rho and Psi windows, the staging tile
     static constexpr int SLOT_BYTES = 9 * TYB * BX * (int)sizeof(T2);
-    static constexpr int RING_OFF = NB * SLOT_BYTES;
-    static constexpr int RING_BYTES = 2 * RING * RX * (int)sizeof(C2);
-    static constexpr int STAGE_OFF = RING_OFF + RING_BYTES;
+    static constexpr int WIN_OFF = NB * SLOT_BYTES;
+    static constexpr int WIN_BYTES = 2 * WIN * RX * (int)sizeof(C2);
+    static constexpr int STAGE_OFF = WIN_OFF + WIN_BYTES;
     static constexpr int STAGE_BYTES = 9 * TY * TX * (int)sizeof(T2);
     static constexpr int SMEM = STAGE_OFF + STAGE_BYTES + 128;
     // observe kernel: one tile box and the rho/Psi tile
@@ -138,7 +182,7 @@ struct Layout {
     static_assert(RX % 32 == 0, "deviation rows are whole warps");
     static_assert((2 * TX * sizeof(T)) % 16 == 0 && (2 * (TX + GX) * sizeof(T)) % 16 == 0,
                   "TMA x coordinates of tiles stay 16-byte aligned");
-    static_assert(SLOT_BYTES % 128 == 0 && RING_BYTES % 128 == 0 && STAGE_BYTES % 128 == 0,
+    static_assert(SLOT_BYTES % 128 == 0 && WIN_BYTES % 128 == 0 && STAGE_BYTES % 128 == 0,
                   "128-byte alignment of the shared-memory regions");
     static_assert((BX * sizeof(T2)) % 16 == 0, "TMA box rows must be 16-byte multiples");
     static_assert(2 * BX <= 256 && 2 * TX <= 256 && BY <= 256, "TMA box extent");
