@@ -30,12 +30,17 @@ import numpy as np  # noqa: E402
 import lbinputs  # noqa: E402
 
 BYTES_PER_SITE = {"fp64": 288, "fp32": 144, "fp16": 72, "bf16": 72}
-KERNEL_SRC = os.path.join(ROOT, "paper_0807_4471_gb300", "csrc", "lb_kernels.cu")
+# the sources that define the step kernel's code
+KERNEL_SRCS = [os.path.join(ROOT, "paper_0807_4471_gb300", "csrc", f)
+               for f in ("lb_kernels.cu", "lb_layout.cuh", "lb_internal.h")]
 
 
 def kernel_hash() -> str:
-    with open(KERNEL_SRC, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for path in KERNEL_SRCS:
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def measured_peaks():

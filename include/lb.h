@@ -55,9 +55,21 @@ typedef enum {
 } lb_status;
 
 /* Storage precision of the populations.  Arithmetic is FP64 for LB_FP64 and
- * FP32 otherwise; the half formats store f_i - w_i rho_ref rounded to
- * nearest-even and decode to FP32. */
+ * FP32 otherwise; every format stores the offsets f_i - w_i rho_ref, and the
+ * half formats decode them to FP32.  LB_FP16_OFFSET stores the offsets times
+ * 2^10 (exact), so that offsets down to 2^-24 keep binary16's full 11-bit
+ * precision; offsets must stay below 64 in magnitude. */
 typedef enum { LB_FP64 = 0, LB_FP32 = 1, LB_FP16_OFFSET = 2, LB_BF16_OFFSET = 3 } lb_precision;
+
+/* Rounding of the half formats when a step stores its populations (FP32 and
+ * FP64 always round to nearest).  LB_ROUND_STOCHASTIC rounds up with
+ * probability equal to the fraction dropped, from a counter-based hash of
+ * (site, step), so results stay reproducible and independent of how lattices
+ * share a launch; round-to-nearest biases slow shear flows (the stored
+ * non-equilibrium part is below one FP16 ulp near the walls), stochastic
+ * rounding does not on average.  FP16 offsets below 2^-24 in magnitude keep
+ * a bias below 2^-34. */
+typedef enum { LB_ROUND_NEAREST = 0, LB_ROUND_STOCHASTIC = 1 } lb_rounding;
 
 /* LB_COUETTE: x periodic, halfway bounce-back walls at y = -1/2 (velocity
  * -u_wall) and y = ny - 1/2 (velocity +u_wall). */
@@ -94,6 +106,8 @@ typedef struct {
     double g_x;                /* uniform body acceleration along x            */
     double kolmo_amp;          /* Kolmogorov acceleration amplitude            */
     double kolmo_k;            /* a_x += kolmo_amp sin(2 pi kolmo_k y / ny)    */
+    int32_t rounding;          /* lb_rounding of the half formats              */
+    int32_t reserved0;         /* must be 0                                    */
 } lb_params;
 
 typedef struct {
@@ -109,7 +123,8 @@ typedef struct {
 } lb_stress_out;
 
 /* Fill *p with the Fig. 2 caption couplings, tau = 1, rho0 = 0.70, a periodic
- * 128 x 128 FP32 lattice, init_amp = 0.03, stress_every = 1. */
+ * 128 x 128 FP32 lattice, init_amp = 0.03, stress_every = 1, stochastic
+ * rounding of the half formats. */
 void lb_params_default(lb_params* p);
 
 /* Device bytes a handle needs for *p (both population buffers and the

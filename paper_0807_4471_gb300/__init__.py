@@ -41,7 +41,8 @@ class lb_params(C.Structure):
         ("G_A2", C.c_double), ("G_B1", C.c_double), ("G_B2", C.c_double),
         ("G_X", C.c_double), ("rho0", C.c_double), ("u_wall", C.c_double),
         ("init_amp", C.c_double), ("rho_ref", C.c_double), ("g_x", C.c_double),
-        ("kolmo_amp", C.c_double), ("kolmo_k", C.c_double),
+        ("kolmo_amp", C.c_double), ("kolmo_k", C.c_double), ("rounding", C.c_int32),
+        ("reserved0", C.c_int32),
     ]
 
 

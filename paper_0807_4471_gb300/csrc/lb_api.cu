@@ -96,6 +96,7 @@ void lb_params_default(lb_params* p) {
     p->G_X = 0.58;
     p->rho0 = 0.70;
     p->init_amp = 0.03;
+    p->rounding = LB_ROUND_STOCHASTIC;
 }
 
 lb_status lb_workspace_size(const lb_params* p, size_t* bytes) {

@@ -38,6 +38,8 @@ lb_status validate_params(const lb_params* p) {
     if (p->force_scheme != LB_FORCE_SHIFT && p->force_scheme != LB_FORCE_SOURCE) return LB_ERR_INVALID;
     if (!(p->tau_A > 0.5) || !(p->tau_B > 0.5) || !(p->rho0 > 0.0)) return LB_ERR_INVALID;
     if (p->stress_every < 1 || p->stress_t0 < 0) return LB_ERR_INVALID;
+    if (p->rounding != LB_ROUND_NEAREST && p->rounding != LB_ROUND_STOCHASTIC) return LB_ERR_INVALID;
+    if (p->reserved0 != 0) return LB_ERR_INVALID;
     const double vals[] = {p->tau_A, p->tau_B, p->G_A1, p->G_A2, p->G_B1, p->G_B2, p->G_X,
                            p->rho0, p->u_wall, p->init_amp, p->rho_ref, p->g_x, p->kolmo_amp,
                            p->kolmo_k};
@@ -143,6 +145,8 @@ static void fill_coef(Coef<C>& k, const lb_params* p) {
     k.g_x = (C)p->g_x;
     k.kolmo_amp = (C)p->kolmo_amp;
     k.kolmo_w = (C)(2.0 * M_PI * p->kolmo_k / p->ny);
+    k.sr = (p->rounding == LB_ROUND_STOCHASTIC &&
+            (p->precision == LB_FP16_OFFSET || p->precision == LB_BF16_OFFSET)) ? 1 : 0;
     k.source = p->force_scheme == LB_FORCE_SOURCE ? 1 : 0;
     k.has_accel = (p->g_x != 0.0 || p->kolmo_amp != 0.0) ? 1 : 0;
 }
@@ -156,6 +160,7 @@ static LatVals<C> vals_of(const Coef<C>& k) {
     v.inv_rho0 = k.inv_rho0;
     v.gx_rho0 = k.gx_rho0;
     v.u_wall = k.u_wall;
+    v.kolmo_w = k.kolmo_w;
     return v;
 }
 

@@ -80,6 +80,7 @@ struct Coef {
     C g_x;             // uniform body acceleration
     C kolmo_amp;       // Kolmogorov acceleration amplitude
     C kolmo_w;         // 2 pi kolmo_k / ny
+    int sr;            // 1: half formats stored with stochastic rounding
     int source;        // 1: additive source term; 0: velocity shift
     int has_accel;     // 1 if g_x or kolmo_amp is nonzero
 };
@@ -88,6 +89,7 @@ struct Coef {
 template <typename C>
 struct LatVals {
     C rho_ref, psi_ref, psi_scale, inv_rho0, gx_rho0, u_wall;
+    C kolmo_w;         // 2 pi kolmo_k / ny (ny is per lattice)
 };
 
 // One lattice of a step launch, in device memory (128-byte aligned for the

@@ -132,7 +132,8 @@ __device__ __forceinline__ C2 sum9(const C2 h[9]) {
                 h[8]);
 }
 
-// The offsets h_i(r, t) of both species at lattice row y, as (A, B) pairs.
+// The offsets h_i(r, t) of both species at lattice row y, as (A, B) pairs,
+// in the storage scale of precision P.
 // bm, b0, bp point at the site's pair in the staged rows y-1, y, y+1 of
 // plane 0 (plane i is PS pairs further).  pull = 1: streamed from
 // h*(r - c_i, t - 1), with halfway bounce-back at the Couette walls:
@@ -158,13 +159,13 @@ __device__ __forceinline__ void load_site(const typename Prec<P>::T2* bm,
             C2 sv[9];
 #pragma unroll
             for (int j = 0; j < 9; ++j) sv[j] = dec2(b0[j * PS]);
-            const C2 rw = padd(pset(v.rho_ref), sum9(sv));
+            const C2 rw = pfma(sum9(sv), pset(inv_scale_of<P>()), pset(v.rho_ref));
             const int up = (y == 0);                 // links arriving upward
             const C uw = up ? -v.u_wall : v.u_wall;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 if ((up && cy(i) == 1) || (!up && cy(i) == -1)) {
-                    const C m = C(6) * wgt<C>(i) * (C(cx(i)) * uw);
+                    const C m = scale_of<P>() * C(6) * wgt<C>(i) * (C(cx(i)) * uw);
                     h[i] = pfma(pset(m), rw, sv[opp(i)]);
                 }
             }
@@ -193,6 +194,7 @@ __device__ __forceinline__ void cell_dev(const typename Prec<P>::T2* bm,
     typename Prec<P>::C2 h[9];
     load_site<P, PS>(bm, b0, bp, y, per, pull, g, v, h);
     r = sum9(h);
+    if constexpr (Prec<P>::SCALE_LOG2 != 0) r = pmul(r, pset(inv_scale_of<P>()));
     q = dpsi_of(r, v);
 }
 
@@ -202,17 +204,18 @@ __device__ __forceinline__ void cell_dev(const typename Prec<P>::T2* bm,
 // heq_i = f^eq_i - w_i rho_ref = w_i [d_rho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u^2)],
 // evaluated per pair (i, opp(i)), whose c.u differ only in sign:
 // heq = E +- O with E = w (d_rho - 1.5 rho u^2 + 4.5 rho (c.u)^2), O = 3 w rho c.u.
+// h and out are in the storage scale SC (a power of two), folded into w.
 template <typename C, typename C2, bool SRC>
 __device__ __forceinline__ void collide(const C2 h[9], C2 out[9], C2 drho, C2 rho, C2 ux, C2 uy,
-                                        C2 om, C2 Fx, C2 Fy) {
+                                        C2 om, C2 Fx, C2 Fy, C SC) {
     const C2 Q = pfma(pmul(rho, pset(C(-1.5))), pfma(ux, ux, pmul(uy, uy)), drho);
-    out[0] = pfma(om, psub(pmul(pset(wgt<C>(0)), Q), h[0]), h[0]);
+    out[0] = pfma(om, psub(pmul(pset(SC * wgt<C>(0)), Q), h[0]), h[0]);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int i = k == 0 ? 1 : (k == 1 ? 2 : (k == 2 ? 5 : 6));   // c.u = ux, uy, ux+uy, uy-ux
         const int j = opp(i);
         const C2 cu = k == 0 ? ux : (k == 1 ? uy : (k == 2 ? padd(ux, uy) : psub(uy, ux)));
-        const C w = wgt<C>(i);
+        const C w = SC * wgt<C>(i);
         const C2 rcu = pmul(rho, cu);
         const C2 E = pmul(pset(w), pfma(pmul(pset(C(4.5)), cu), rcu, Q));
         const C2 O = pmul(pset(C(3) * w), rcu);
@@ -232,6 +235,7 @@ struct SiteOut {
     T2* stage;             // staging tile slot of the site (full tiles), or null
     T2* fout;              // output buffer (ragged tiles and ghost copies)
     bool edge;             // the tile may hold sites with periodic ghost copies
+    uint32_t key;          // stochastic rounding: hash of the lattice's step
     int obs;               // ObsKind (observe kernel) or OBS_NONE
     double* obs_out;
     int q0, q1;
@@ -259,8 +263,12 @@ __device__ __forceinline__ void site_update(
     const C2 rho = padd(pset(v.rho_ref), drho);
     // sum_i w_i c_i = 0, so the offsets carry all of j
     const C2 d57 = psub(h[5], h[7]), d68 = psub(h[6], h[8]);
-    const C2 jx = padd(psub(h[1], h[3]), psub(d57, d68));
-    const C2 jy = padd(psub(h[2], h[4]), padd(d57, d68));
+    C2 jx = padd(psub(h[1], h[3]), psub(d57, d68));
+    C2 jy = padd(psub(h[2], h[4]), padd(d57, d68));
+    if constexpr (Prec<P>::SCALE_LOG2 != 0) {
+        jx = pmul(jx, pset(inv_scale_of<P>()));
+        jy = pmul(jy, pset(inv_scale_of<P>()));
+    }
     if (!(isfinite(rho.x) && isfinite(rho.y))) bad = true;
 
     // Eq. (2): F_s = -Psi_s(r) sum_d K_s(d) d [Psi_s(r+d) - Psi_s(r-d)]
@@ -293,7 +301,7 @@ __device__ __forceinline__ void site_update(
     C2 Fy = pfma(npc, padd(ay1, ay2), pmul(ng, pair(qy.y, qy.x)));
     if (GEN && k.has_accel) {
         C acc = k.g_x;
-        if (k.kolmo_amp != C(0)) acc += k.kolmo_amp * csin(k.kolmo_w * C(y));
+        if (k.kolmo_amp != C(0)) acc += k.kolmo_amp * csin(v.kolmo_w * C(y));
         Fx = pfma(rho, pset(acc), Fx);
     }
 
@@ -315,7 +323,7 @@ __device__ __forceinline__ void site_update(
             for (int q = 0; q < 18; ++q)
                 if (q >= o.q0 && q < o.q1)
                     o.obs_out[(long long)(q - o.q0) * N + idx] =
-                        (double)(q < 9 ? h[q % 9].x : h[q % 9].y) +
+                        (double)(q < 9 ? h[q % 9].x : h[q % 9].y) * (double)inv_scale_of<P>() +
                         wgt<double>(q % 9) * (double)v.rho_ref;
         }
         red[0] += rA;
@@ -343,12 +351,23 @@ __device__ __forceinline__ void site_update(
     }
     C2 hs[9];
     if (source)
-        collide<C, C2, true>(h, hs, drho, rho, ux, uy, om, Fx, Fy);
+        collide<C, C2, true>(h, hs, drho, rho, ux, uy, om, Fx, Fy, scale_of<P>());
     else
-        collide<C, C2, false>(h, hs, drho, rho, ux, uy, om, Fx, Fy);
+        collide<C, C2, false>(h, hs, drho, rho, ux, uy, om, Fx, Fy, scale_of<P>());
     T2 e[9];
+    if constexpr (sizeof(T2) == 4) {
+        if (k.sr) {   // half formats: random bits from (site, step), one word per pair
+            const uint32_t r = hash32(o.key ^ (uint32_t)(y * g.nx + x));
 #pragma unroll
-    for (int i = 0; i < 9; ++i) e[i] = enc2<T2, C>(hs[i].x, hs[i].y);
+            for (int i = 0; i < 9; ++i) e[i] = enc2_sr<T2>(hs[i], r * sr_mult(i));
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) e[i] = enc2<T2, C>(hs[i].x, hs[i].y);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) e[i] = enc2<T2, C>(hs[i].x, hs[i].y);
+    }
 
     // Full tiles go through the staging tile and a bulk tensor store; ragged
     // tiles and periodic ghost copies use plain stores.
@@ -383,7 +402,7 @@ __device__ __forceinline__ void site_update(
         const C uw = down ? -v.u_wall : v.u_wall;
         C2 sv[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) sv[i] = dec2(e[i]);
+        for (int i = 0; i < 9; ++i) sv[i] = pmul(dec2(e[i]), pset(inv_scale_of<P>()));
         const C2 rw2 = padd(pset(v.rho_ref), sum9(sv));
         const C rw[2] = {rw2.x, rw2.y};
 #pragma unroll
@@ -531,6 +550,8 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
         const bool per = ALLPER || g.periodic;
         const int cur = *((volatile int*)&d->st->cur);
         const int pull = *((volatile int*)&d->st->pull);
+        // the step counter advances only after every CTA of the launch is done
+        const uint32_t key = hash32((uint32_t)*((volatile long long*)&d->st->t) * 0x9e3779b9u);
         T2* fout = reinterpret_cast<T2*>(d->fbuf[cur ^ 1]);
         double wall[2] = {0.0, 0.0};
         for (int ty = ty_a; ty < ty_b; ++ty) {
@@ -624,6 +645,7 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
                     o.stage = full ? stage + ly * L::TX + lx : nullptr;
                     o.fout = fout;
                     o.edge = edge;
+                    o.key = key;
                     o.obs = OBS_NONE;
                     double wr[4] = {0.0, 0.0, 0.0, 0.0};
                     site_update<P, false, GEN, PS>(brow(ly + 2, bc), brow(ly + 3, bc), brow(ly + 4, bc),
@@ -738,6 +760,7 @@ __global__ void __launch_bounds__(Layout<P>::NT)
     v.inv_rho0 = a.k.inv_rho0;
     v.gx_rho0 = a.k.gx_rho0;
     v.u_wall = a.k.u_wall;
+    v.kolmo_w = a.k.kolmo_w;
     if (tid == 0) {
         s_fail = 0;
         mbar_init(&bar, 1);
@@ -793,6 +816,7 @@ __global__ void __launch_bounds__(Layout<P>::NT)
             o.stage = nullptr;
             o.fout = nullptr;
             o.edge = false;
+            o.key = 0u;
             o.obs = a.obs;
             o.obs_out = a.obs_out;
             o.q0 = a.q0;
@@ -868,8 +892,9 @@ __global__ void k_init(Geom g, Coef<typename Prec<P>::C> k, typename Prec<P>::T2
             const double cu = cx(i) * ux + cy(i) * uy;
             const double e = 3.0 * cu + 4.5 * cu * cu - 1.5 * usq;
             // f^eq_i - w_i rho_ref for both species
-            const double hA = wgt<double>(i) * ((r[0] - rref) + r[0] * e);
-            const double hB = wgt<double>(i) * ((r[1] - rref) + r[1] * e);
+            const double sc = (double)scale_of<P>();
+            const double hA = sc * wgt<double>(i) * ((r[0] - rref) + r[0] * e);
+            const double hB = sc * wgt<double>(i) * ((r[1] - rref) + r[1] * e);
             put2<T2>(fout, g, i, x, y, encd2<T2>(hA, hB));
         }
     }
@@ -889,8 +914,8 @@ __global__ void k_load_pops(Geom g, typename Prec<P>::C rho_ref, typename Prec<P
         const int x = (int)(idx % g.nx), y = (int)(idx / g.nx);
         for (int i = i0; i < i1; ++i) {
             const double* src = pops + (long long)(i - i0) * 2 * N;
-            const double off = wgt<double>(i) * rref;
-            put2<T2>(fout, g, i, x, y, encd2<T2>(src[idx] - off, src[N + idx] - off));
+            const double off = wgt<double>(i) * rref, sc = (double)scale_of<P>();
+            put2<T2>(fout, g, i, x, y, encd2<T2>(sc * (src[idx] - off), sc * (src[N + idx] - off)));
         }
     }
 }

@@ -32,26 +32,38 @@ __device__ __forceinline__ C wgt(int i) {
 template <int P> struct Prec;
 // TX: tile width, chosen so that a deviation row with its 2-cell halo,
 // TX + 4, is a multiple of 32 (one cell per thread); NB: ring slots of
-// 8-row population blocks in the step kernel.
+// 8-row population blocks in the step kernel.  SCALE_LOG2: the stored value
+// is the offset times 2^SCALE_LOG2 (FP16: 2^10, which keeps offsets down to
+// 2^-24 in binary16's normal range, where rounding has its full 11 bits;
+// the largest storable offset becomes 64).
 template <> struct Prec<LB_FP64> {
     typedef double T; typedef double2 T2; typedef double C; typedef double2 C2;
-    static constexpr int GX = 4, TX = 28, TY = 8, NB = 3;
+    static constexpr int GX = 4, TX = 28, TY = 8, NB = 3, SCALE_LOG2 = 0;
 };
 template <> struct Prec<LB_FP32> {
     typedef float T; typedef float2 T2; typedef float C; typedef float2 C2;
-    static constexpr int GX = 4, TX = 60, TY = 8, NB = 4;
+    static constexpr int GX = 4, TX = 60, TY = 8, NB = 4, SCALE_LOG2 = 0;
 };
 template <> struct Prec<LB_FP16_OFFSET> {
     typedef __half T; typedef __half2 T2; typedef float C; typedef float2 C2;
-    static constexpr int GX = 8, TX = 60, TY = 8, NB = 4;
+    static constexpr int GX = 8, TX = 60, TY = 8, NB = 4, SCALE_LOG2 = 10;
 };
 template <> struct Prec<LB_BF16_OFFSET> {
     typedef __nv_bfloat16 T; typedef __nv_bfloat162 T2; typedef float C; typedef float2 C2;
-    static constexpr int GX = 8, TX = 60, TY = 8, NB = 4;
+    static constexpr int GX = 8, TX = 60, TY = 8, NB = 4, SCALE_LOG2 = 0;
 };
+// The storage scale of precision P and its inverse, in the compute type.
+template <int P> __host__ __device__ constexpr typename Prec<P>::C scale_of() {
+    return typename Prec<P>::C(1 << Prec<P>::SCALE_LOG2);
+}
+template <int P> __host__ __device__ constexpr typename Prec<P>::C inv_scale_of() {
+    return typename Prec<P>::C(1) / typename Prec<P>::C(1 << Prec<P>::SCALE_LOG2);
+}
 
 // Stored values are offsets h_i = f_i - w_i rho_ref from the lattice weights
-// (all precisions).  The codecs only convert between storage and compute type.
+// (all precisions), times the storage scale of the precision.  The codecs
+// only convert between storage and compute type; the kernels work on the
+// scaled offsets and fold the scale into their constants.
 __device__ __forceinline__ double2 dec2(double2 v) { return v; }
 __device__ __forceinline__ float2 dec2(float2 v) { return v; }
 __device__ __forceinline__ float2 dec2(__half2 v) { return __half22float2(v); }
@@ -70,6 +82,46 @@ template <> __device__ __forceinline__ __half2 enc2<__half2, float>(float a, flo
 template <> __device__ __forceinline__ __nv_bfloat162 enc2<__nv_bfloat162, float>(float a, float b) {
     return __floats2bfloat162_rn(a, b);
 }
+// Stochastic rounding of an FP32 pair to a 16-bit format: adding a uniform
+// random integer below 2^d to the bit pattern of |v| and truncating the d low
+// bits (round toward zero) rounds away from zero with probability equal to
+// the dropped fraction.  d = 13 for FP16 (exact for its normal range; below
+// 2^-14 more bits are dropped and the result leans toward zero by less than
+// one subnormal ulp), d = 16 for BF16.  r holds 32 random bits.
+template <typename T2> __device__ __forceinline__ T2 enc2_sr(float2 v, uint32_t r);
+template <> __device__ __forceinline__ __half2 enc2_sr<__half2>(float2 v, uint32_t r) {
+    const float a = __uint_as_float(__float_as_uint(v.x) + (r >> 19));
+    const float b = __uint_as_float(__float_as_uint(v.y) + (r & 0x1fffu));
+    uint32_t d;
+    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));   // high half = b
+    return *reinterpret_cast<const __half2*>(&d);
+}
+template <> __device__ __forceinline__ __nv_bfloat162 enc2_sr<__nv_bfloat162>(float2 v, uint32_t r) {
+    const uint32_t a = __float_as_uint(v.x) + (r >> 16);
+    const uint32_t b = __float_as_uint(v.y) + (r & 0xffffu);
+    const uint32_t d = __byte_perm(a, b, 0x7632);   // low half = a's high half, high half = b's
+    return *reinterpret_cast<const __nv_bfloat162*>(&d);
+}
+
+// 32-bit integer hash (the "lowbias32" finaliser of C. Wellons: two
+// multiply-xorshift rounds).  The nine random words of a site are the
+// site's hash times nine odd constants (a bijection each, so every word is
+// uniform; only their mutual independence is approximate, which does not
+// bias the rounding).
+__device__ __forceinline__ uint32_t hash32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+__host__ __device__ constexpr uint32_t sr_mult(int i) {
+    return i == 0 ? 0x9e3779b1u : i == 1 ? 0x85ebca77u : i == 2 ? 0xc2b2ae3du
+         : i == 3 ? 0x27d4eb2fu : i == 4 ? 0x165667b1u : i == 5 ? 0xd3a2646du
+         : i == 6 ? 0xfd7046c5u : i == 7 ? 0xb55a4f09u : 0x6a09e667u;
+}
+
 // Encoding of offsets computed in double (initialisation).
 template <typename T2> __device__ __forceinline__ T2 encd2(double a, double b);
 template <> __device__ __forceinline__ double2 encd2<double2>(double a, double b) {

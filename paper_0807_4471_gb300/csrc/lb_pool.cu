@@ -110,7 +110,7 @@ bool same_shared(const lb_params& a, const lb_params& b) {
            a.force_scheme == b.force_scheme && a.tau_A == b.tau_A && a.tau_B == b.tau_B &&
            a.G_A1 == b.G_A1 && a.G_A2 == b.G_A2 && a.G_B1 == b.G_B1 && a.G_B2 == b.G_B2 &&
            a.G_X == b.G_X && a.g_x == b.g_x && a.kolmo_amp == b.kolmo_amp &&
-           a.kolmo_k == b.kolmo_k;
+           a.kolmo_k == b.kolmo_k && a.rounding == b.rounding;
 }
 
 std::string signature(lb_pool* P) {

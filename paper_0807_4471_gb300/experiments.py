@@ -255,3 +255,94 @@ def couette_ensemble(lb, rate: float, seeds, precision: str = "fp32", n: int = 2
         while pool.run(10_000):
             pass
         return [float(pool.stress(j)["sigma_mean"]) for j in jobs]
+
+
+def ensemble_statistics(lb, precision: str, seeds, n: int = 128, steps: int = 2000, **kw):
+    """Per-seed domain length and phi variance after `steps` steps of seeded
+    periodic lattices stepped together in one pool."""
+    p = lb.make_params(n, n, precision, **kw)
+    budget = lb.Pool.footprint(p) * len(seeds) + (64 << 20)
+    L, var = [], []
+    with lb.Pool(p, budget, max_jobs=len(seeds)) as pool:
+        jobs = [pool.admit(p, int(s), steps) for s in seeds]
+        pool.run(steps)
+        for j in jobs:
+            ra, rb, _, _ = pool.fields(j)
+            phi = ra - rb
+            L.append(domain_length(phi))
+            k, s, c = structure_factor(phi)
+            var.append(float((s * c).sum()))
+    return dict(L=L, var=var)
+
+
+# ------------------------------------------------------------ command line
+def main(argv=None):
+    """Run one study on the GPU and print its result as JSON:
+
+        python -m paper_0807_4471_gb300.experiments kolmogorov --psi-form 1
+        python -m paper_0807_4471_gb300.experiments ageing
+        python -m paper_0807_4471_gb300.experiments laplace
+        python -m paper_0807_4471_gb300.experiments couette --precisions fp64,fp32,fp16,bf16
+        python -m paper_0807_4471_gb300.experiments couette-ensemble --rate 1e-4
+        python -m paper_0807_4471_gb300.experiments statistics --steps 2000
+    """
+    import argparse
+    import json
+
+    import paper_0807_4471_gb300 as lb
+
+    ap = argparse.ArgumentParser(prog="python -m paper_0807_4471_gb300.experiments")
+    ap.add_argument("study", choices=["kolmogorov", "ageing", "laplace", "couette",
+                                      "couette-ensemble", "statistics"])
+    ap.add_argument("--psi-form", type=int, default=1)
+    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--precisions", default="fp64,fp32,fp16,bf16")
+    ap.add_argument("--rounding", type=int, default=1)
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--every", type=int, default=20_000)
+    ap.add_argument("--U0", type=float, default=None)
+    ap.add_argument("--seeds", type=int, default=16)
+    ap.add_argument("--rate", type=float, default=1e-4)
+    ap.add_argument("--rho0s", default="0.55,0.60,0.65,0.70,0.75,0.80")
+    ap.add_argument("--passive", action="store_true", help="all couplings zero")
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args(argv)
+    lb.load()
+    kw = dict(psi_form=a.psi_form, rounding=a.rounding)
+    if a.passive:
+        kw.update(G_A1=0.0, G_A2=0.0, G_B1=0.0, G_B2=0.0, G_X=0.0, init_amp=0.0)
+    precs = a.precisions.split(",")
+    if a.study == "kolmogorov":
+        res = kolmogorov_run(lb, n=a.n or 128, U0=0.1 if a.U0 is None else a.U0,
+                             steps=a.steps or 2_000_000, every=a.every, precision=a.precision, **kw)
+    elif a.study == "ageing":
+        taus = [0, 1000, 3000, 10_000, 30_000, 100_000, 200_000]
+        out = {}
+        for U0 in ((0.02, 0.03) if a.U0 is None else (a.U0,)):
+            t, C = ageing_overlap(lb, a.n or 128, range(a.seeds), [50_000, 200_000, 300_000], taus,
+                                  precision=a.precision, U0=U0, **kw)
+            out[str(U0)] = dict(t_w=[50_000, 200_000, 300_000], taus=t, C=C.tolist())
+        res = out
+    elif a.study == "laplace":
+        res = {r0: laplace_test(lb, float(r0), precision=a.precision, **kw)
+               for r0 in a.rho0s.split(",")}
+    elif a.study == "couette":
+        rates = [float(v) for v in np.logspace(-6, -4, 8)]
+        res = couette_study(lb, rates, precisions=tuple(precs), n=a.n or 512,
+                            steps=a.steps or 200_000, avg_from=(a.steps or 200_000) // 2, **kw)
+    elif a.study == "couette-ensemble":
+        res = {p: couette_ensemble(lb, a.rate, range(a.seeds), precision=p, n=a.n or 256,
+                                   steps=a.steps or 100_000, **kw) for p in precs}
+    else:
+        res = {p: ensemble_statistics(lb, p, range(32 if a.seeds == 16 else a.seeds),
+                                      n=a.n or 128, steps=a.steps or 2000, **kw) for p in precs}
+    text = json.dumps(res)
+    if a.out:
+        with open(a.out, "w") as fh:
+            fh.write(text)
+    print(text)
+
+
+if __name__ == "__main__":
+    main()

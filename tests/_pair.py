@@ -43,8 +43,10 @@ def rel_err(a, b):
 
 
 def round_half(x):
-    """Round FP64 values to IEEE binary16, nearest-even (numpy's conversion)."""
-    return np.asarray(x, dtype=np.float64).astype(np.float16).astype(np.float64)
+    """Round FP64 offsets to the FP16 storage format: binary16 of x * 2^10,
+    nearest-even (numpy's conversion), divided back by 2^10."""
+    x = np.asarray(x, dtype=np.float64) * 1024.0
+    return x.astype(np.float16).astype(np.float64) / 1024.0
 
 
 def round_bf16(x):
@@ -57,12 +59,13 @@ def round_bf16(x):
 
 
 def ulp16(x, fmt):
-    """Spacing of the 16-bit format at |x| (binary16: 10 fraction bits,
-    subnormal spacing 2^-24; bfloat16: 7 fraction bits)."""
+    """Spacing of the 16-bit storage format at |x| (FP16: binary16 of
+    x * 2^10, 10 fraction bits, subnormal spacing 2^-34 in x; bfloat16: 7
+    fraction bits)."""
     ax = np.maximum(np.abs(np.asarray(x, dtype=np.float64)), 1e-300)
     e = np.floor(np.log2(ax))
     if fmt == "fp16":
-        return np.power(2.0, np.maximum(e, -14.0) - 10.0)
+        return np.power(2.0, np.maximum(e, -24.0) - 10.0)
     return np.power(2.0, e - 7.0)
 
 

@@ -201,17 +201,24 @@ def test_nonfinite_is_reported(lb):
 # ----------------------------------------------------------- FP16 / BF16
 @pytest.mark.parametrize("fmt", ["fp16", "bf16"])
 @pytest.mark.parametrize("boundary", [0, 1])
-def test_half_offset_one_step(lb, O, fmt, boundary):
+@pytest.mark.parametrize("rounding", [0, 1])
+def test_half_offset_one_step(lb, O, fmt, boundary, rounding):
     """One step from the same quantised state: the oracle advances the
     quantised initial populations in FP64 and the result is compared, as
-    offsets h = f - w_i rho_ref, with the GPU's 16-bit output: at most one
-    unit in the last place of the format (FP32 arithmetic, one rounding)."""
+    offsets h = f - w_i rho_ref, with the GPU's 16-bit output (FP32
+    arithmetic, one rounding).  Nearest: within one unit in the last place of
+    the format.  Stochastic: one of the two neighbours of the exact value, and
+    the number rounded up matches the sum of the dropped fractions (each
+    neighbour is taken with the probability that makes the rounding
+    unbiased) within five standard deviations."""
     from _pair import offsets, round_bf16, round_half, ulp16
     rnd = round_half if fmt == "fp16" else round_bf16
     m = model(72, 40, boundary=boundary, u_wall=0.02 if boundary else 0.0)
     P = oracle_params(O, m)
     rref = float(np.float32(m["rho0"]))       # offsets are taken from rho_ref in FP32
-    g = lb.Lattice(gpu_params(lb, m, fmt)).init_seeded(6)
+    p = gpu_params(lb, m, fmt)
+    p.rounding = rounding
+    g = lb.Lattice(p).init_seeded(6)
     f0 = O.init_seeded(P, 6)
     w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
     h0 = rnd(offsets(f0, rref))
@@ -222,7 +229,23 @@ def test_half_offset_one_step(lb, O, fmt, boundary):
     want = offsets(f, rref)
     got = offsets(gpu_pops_as_oracle(g.populations()), rref)
     err = np.abs(got - want)
-    assert (err <= ulp16(want, fmt) * 1.0 + 1e-9).all(), err.max()
+    u = ulp16(want, fmt)
+    if rounding == 0:
+        assert (err <= u * 1.0 + 1e-9).all(), err.max()
+    else:
+        # (1e-9: FP32 arithmetic error of offsets that nearly cancel)
+        assert (err <= u * (1 + 1e-3) + 1e-9).all(), (err / u).max()
+        lo = np.where(rnd(want) <= want, rnd(want), rnd(want) - u)   # neighbour toward -inf
+        frac = np.clip((want - lo) / u, 0.0, 1.0)
+        up = got > lo + 0.5 * u
+        # values not already on the grid (and, in FP16, in its normal range)
+        inner = (frac > 1e-3) & (frac < 1 - 1e-3)
+        if fmt == "fp16":
+            inner &= np.abs(want) >= 2.0 ** -24
+        n_up, expect = up[inner].sum(), frac[inner].sum()
+        sd = np.sqrt((frac[inner] * (1 - frac[inner])).sum())
+        assert inner.sum() > 1000
+        assert abs(n_up - expect) < 5 * sd, (n_up, expect, sd)
     g.close()
 
 
