@@ -251,7 +251,9 @@ lb_status lb_pool_stress(lb_pool* pool, lb_job job, lb_stress_out* out);
 /* Free a member's arena space (finished or not). */
 lb_status lb_pool_release(lb_pool* pool, lb_job job);
 
-/* Tiles per work item the current member set runs with (0 if none). */
+/* Work partition the current member set runs with: > 0, segments of that
+ * many tiles dealt to the CTAs in turn; -1, one contiguous run of tiles per
+ * CTA; 0 if none is built. */
 int32_t lb_pool_segment(const lb_pool* pool);
 
 lb_status lb_pool_destroy(lb_pool* pool);

@@ -30,7 +30,8 @@ struct HandleLayout {
 HandleLayout handle_layout(const lb_params* p) {
     HandleLayout H;
     const int tx = kernel_tile_x(p->precision), ty = kernel_tile_y(p->precision);
-    const size_t ntiles = (size_t)((p->nx + tx - 1) / tx) * (size_t)((p->ny + ty - 1) / ty);
+    const size_t nstrips = (size_t)((p->nx + tx - 1) / tx);
+    const size_t ntiles = nstrips * (size_t)((p->ny + ty - 1) / ty);
     size_t off = 0;
     H.lattice = off;
     off = align_up(off + lattice_bytes(p), kAlign);
@@ -39,7 +40,8 @@ HandleLayout handle_layout(const lb_params* p) {
     H.desc = off;
     off = align_up(off + sizeof(LatDesc<double>), kAlign);
     H.slots = off;
-    off = align_up(off + sizeof(double) * 2 * ntiles, kAlign);   // seg >= 1: items <= tiles
+    // wall slots and item tables (items <= tiles; up to 1024 CTAs)
+    off = align_up(off + sizeof(double) * launch_area_doubles(ntiles, nstrips, 1024), kAlign);
     H.total = off;
     return H;
 }

@@ -270,7 +270,7 @@ int choose_seg(const int* nstrips, const int* ntiles_y, int nlat, int G) {
 }
 
 template <typename C>
-static void fill_desc(LatDesc<C>& d, const Lattice& L, const Coef<C>& k, int item0) {
+static void fill_desc(LatDesc<C>& d, const Lattice& L, const Coef<C>& k, int wall0) {
     memset(&d, 0, sizeof(d));
     for (int b = 0; b < 2; ++b) {
         d.tin[b] = L.tblock[b];
@@ -280,18 +280,84 @@ static void fill_desc(LatDesc<C>& d, const Lattice& L, const Coef<C>& k, int ite
     d.g = L.g;
     d.v = vals_of(k);
     d.st = L.st;
-    d.item0 = item0;
+    d.wall0 = wall0;
     d.nstrips = L.nstrips;
     d.ntiles_y = L.ntiles_y;
-    d.seg = L.seg;
     d.stress_every = L.p.stress_every;
     d.stress_t0 = L.p.stress_t0;
 }
 
-int launch_items(Lattice* const* lats, int nlat, int seg) {
-    int items = 0;
-    for (int l = 0; l < nlat; ++l) items += lats[l]->nstrips * ((lats[l]->ntiles_y + seg - 1) / seg);
-    return items;
+size_t launch_area_doubles(size_t tiles, size_t strips, int sms) {
+    // wall slots (2 per item) | items (int4) | CTA offsets | wall item lists
+    return 2 * tiles + 2 * tiles + ((size_t)sms + 2) / 2 + strips + 8;
+}
+
+namespace {
+
+struct Item {
+    int lat, strip, ty_a, ty_b;
+};
+
+// seg > 0: segments of seg tiles, numbered lattice by lattice, segment row by
+// segment row, strip by strip; CTA b takes items b, b + G, ...
+// seg < 0: the tiles of all lattices in strip order (lattice, strip, tile
+// row) cut into G contiguous runs of equal length (+-1 tile), each run cut
+// again at strip boundaries: every CTA walks one or two strips.
+void partition(Lattice* const* lats, int nlat, int seg, int sms, std::vector<Item>& items,
+               std::vector<int>& cta, int* grid) {
+    items.clear();
+    cta.clear();
+    long long tiles = 0;
+    for (int l = 0; l < nlat; ++l) tiles += (long long)lats[l]->nstrips * lats[l]->ntiles_y;
+    if (seg > 0) {
+        std::vector<Item> all;
+        for (int l = 0; l < nlat; ++l) {
+            const int ns = lats[l]->nstrips, nt = lats[l]->ntiles_y;
+            for (int a = 0; a < nt; a += seg)
+                for (int sx = 0; sx < ns; ++sx) all.push_back({l, sx, a, std::min(a + seg, nt)});
+        }
+        const int G = (int)std::min<long long>((long long)all.size(), sms);
+        for (int b = 0; b < G; ++b) {
+            cta.push_back((int)items.size());
+            for (size_t k = (size_t)b; k < all.size(); k += (size_t)G) items.push_back(all[k]);
+        }
+        cta.push_back((int)items.size());
+        *grid = G;
+        return;
+    }
+    const int G = (int)std::min<long long>(tiles, sms);
+    long long pos = 0;   // global tile index of (l, sx, ty)
+    int l = 0, sx = 0, ty = 0;
+    for (int b = 0; b < G; ++b) {
+        cta.push_back((int)items.size());
+        long long end = tiles * (b + 1) / G;
+        while (pos < end) {
+            const int nt = lats[l]->ntiles_y;
+            const int take = (int)std::min<long long>(nt - ty, end - pos);
+            items.push_back({l, sx, ty, ty + take});
+            pos += take;
+            ty += take;
+            if (ty == nt) {
+                ty = 0;
+                if (++sx == lats[l]->nstrips) {
+                    sx = 0;
+                    ++l;
+                }
+            }
+        }
+    }
+    cta.push_back((int)items.size());
+    *grid = G;
+}
+
+}  // namespace
+
+int launch_items(Lattice* const* lats, int nlat, int seg, int sms) {
+    std::vector<Item> items;
+    std::vector<int> cta;
+    int grid = 0;
+    partition(lats, nlat, seg, sms, items, cta, &grid);
+    return (int)items.size();
 }
 
 lb_status launch_build(Launch& Ln, Lattice* const* lats, int nlat, void* descs, double* slots,
@@ -301,38 +367,69 @@ lb_status launch_build(Launch& Ln, Lattice* const* lats, int nlat, void* descs, 
     const int prec = lats[0]->p.precision;
     std::vector<int> ns((size_t)nlat), nt((size_t)nlat);
     bool allper = true, gen = false;
+    long long tiles = 0, strips = 0;
     for (int l = 0; l < nlat; ++l) {
         ns[(size_t)l] = lats[l]->nstrips;
         nt[(size_t)l] = lats[l]->ntiles_y;
         allper = allper && lats[l]->g.periodic;
         gen = gen || lats[l]->kd.source || lats[l]->kd.has_accel;
+        tiles += (long long)lats[l]->nstrips * lats[l]->ntiles_y;
+        strips += lats[l]->nstrips;
     }
-    const int seg = forced_seg > 0 ? forced_seg : choose_seg(ns.data(), nt.data(), nlat, sms);
-    int items = 0;
+    const int seg = forced_seg != 0 ? forced_seg : choose_seg(ns.data(), nt.data(), nlat, sms);
+    std::vector<Item> items;
+    std::vector<int> cta;
+    int grid = 0;
+    partition(lats, nlat, seg, sms, items, cta, &grid);
+    const int nitems = (int)items.size();
+    // wall item lists: per lattice, the bottom items by strip, then the top ones
+    std::vector<int> wall((size_t)(2 * strips), -1), wall0((size_t)nlat);
+    for (int l = 0, off = 0; l < nlat; ++l) {
+        wall0[(size_t)l] = off;
+        off += 2 * ns[(size_t)l];
+    }
+    for (int k = 0; k < nitems; ++k) {
+        const Item& w = items[(size_t)k];
+        if (w.ty_a == 0) wall[(size_t)(wall0[(size_t)w.lat] + w.strip)] = k;
+        if (w.ty_b == nt[(size_t)w.lat]) wall[(size_t)(wall0[(size_t)w.lat] + ns[(size_t)w.lat] + w.strip)] = k;
+    }
     const size_t dsz = prec == LB_FP64 ? sizeof(LatDesc<double>) : sizeof(LatDesc<float>);
     char* hs = reinterpret_cast<char*>(host_scratch);
     for (int l = 0; l < nlat; ++l) {
         lats[l]->seg = seg;
         if (prec == LB_FP64)
-            fill_desc(*reinterpret_cast<LatDesc<double>*>(hs + l * dsz), *lats[l], lats[l]->kd, items);
+            fill_desc(*reinterpret_cast<LatDesc<double>*>(hs + l * dsz), *lats[l], lats[l]->kd, wall0[(size_t)l]);
         else
-            fill_desc(*reinterpret_cast<LatDesc<float>*>(hs + l * dsz), *lats[l], lats[l]->kf, items);
-        items += lats[l]->nstrips * ((lats[l]->ntiles_y + seg - 1) / seg);
+            fill_desc(*reinterpret_cast<LatDesc<float>*>(hs + l * dsz), *lats[l], lats[l]->kf, wall0[(size_t)l]);
     }
+    // device tables after the wall slots: items (16-byte aligned), CTA offsets, wall lists
+    int4* d_items = reinterpret_cast<int4*>(slots + 2 * (size_t)nitems);
+    int* d_cta = reinterpret_cast<int*>(d_items + nitems);
+    int* d_wall = d_cta + (grid + 1);
+    static_assert(sizeof(Item) == sizeof(int4), "item layout");
     cudaError_t e = cudaMemcpyAsync(descs, hs, dsz * nlat, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);   // host_scratch is reused
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * (size_t)nitems, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_cta, cta.data(), sizeof(int) * cta.size(), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_wall, wall.data(), sizeof(int) * wall.size(), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);   // host buffers are reused
     if (e != cudaSuccess) return cuda_status(e);
     Ln.precision = prec;
     Ln.variant = (allper ? 1 : 0) | (gen ? 2 : 0);
-    Ln.grid = dim3((unsigned)(items < sms ? items : sms), 1, 1);
-    Ln.nitems = items;
+    Ln.grid = dim3((unsigned)grid, 1, 1);
+    Ln.nitems = nitems;
     Ln.seg = seg;
     if (prec == LB_FP64) {
         BatchArgs<double>& a = Ln.ad;
         a.k = lats[0]->kd;
         a.lat = reinterpret_cast<const LatDesc<double>*>(descs);
         a.nlat = nlat;
-        a.nitems = items;
+        a.nitems = nitems;
+        a.items = d_items;
+        a.cta_items = d_cta;
+        a.wall_items = d_wall;
         a.slots = slots;
         a.ticket = ticket;
     } else {
@@ -340,7 +437,10 @@ lb_status launch_build(Launch& Ln, Lattice* const* lats, int nlat, void* descs, 
         a.k = lats[0]->kf;
         a.lat = reinterpret_cast<const LatDesc<float>*>(descs);
         a.nlat = nlat;
-        a.nitems = items;
+        a.nitems = nitems;
+        a.items = d_items;
+        a.cta_items = d_cta;
+        a.wall_items = d_wall;
         a.slots = slots;
         a.ticket = ticket;
     }

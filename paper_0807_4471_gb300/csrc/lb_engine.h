@@ -57,12 +57,16 @@ int choose_seg(const int* nstrips, const int* ntiles_y, int nlat, int G);
 // for nlat LatDesc<double>) through `host_scratch` (as large, host) and fill
 // the launch.  Synchronises the stream.  All lattices share the precision
 // and the coefficients of lats[0] (couplings, tau, forcing).  seg > 0 forces
-// the segment length; seg = 0 takes choose_seg's.
+// the segment length; seg = 0 takes choose_seg's; seg < 0 cuts the tiles
+// into one contiguous run per CTA.  `slots` holds launch_area_doubles(tiles,
+// strips, sms) doubles for the lattices' total tiles and strips: the per-item
+// wall slots and the item tables.
 lb_status launch_build(Launch& Ln, Lattice* const* lats, int nlat, void* descs, double* slots,
                        unsigned int* ticket, int sms, cudaStream_t stream, void* host_scratch,
                        int seg = 0);
 // Work items of a launch over lats with segment length seg.
-int launch_items(Lattice* const* lats, int nlat, int seg);
+int launch_items(Lattice* const* lats, int nlat, int seg, int sms);
+size_t launch_area_doubles(size_t tiles, size_t strips, int sms);
 lb_status launch_run(const Launch& Ln, cudaStream_t s);
 
 lb_status lattice_init_seeded(Lattice& L, uint64_t seed, cudaStream_t s);

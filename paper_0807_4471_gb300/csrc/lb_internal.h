@@ -103,10 +103,9 @@ struct alignas(128) LatDesc {
     LatVals<C> v;
     void* fbuf[2];
     DevStats* st;
-    int item0;             // first work item of this lattice in the launch
+    int wall0;             // this lattice's wall items: wall_items[wall0 .. wall0 + 2 nstrips)
     int nstrips;           // ceil(nx / TX)
     int ntiles_y;          // ceil(ny / TY)
-    int seg;               // tiles per work item (a segment of a column strip)
     int stress_every;
     long long stress_t0;
 };
@@ -115,9 +114,16 @@ struct alignas(128) LatDesc {
 template <typename C>
 struct BatchArgs {
     Coef<C> k;                  // coefficients shared by all lattices of the launch
-    const LatDesc<C>* lat;      // nlat descriptors, ordered by item0
+    const LatDesc<C>* lat;      // nlat descriptors
     int nlat;
     int nitems;                 // total work items
+    // Work items (lattice, strip, first tile row, end tile row), grouped by
+    // CTA: CTA b takes items cta_items[b] .. cta_items[b + 1] - 1 in order.
+    const int4* items;
+    const int* cta_items;
+    // Per lattice, the items holding its bottom wall row (strip order), then
+    // those holding its top wall row: the wall sums are taken in this order.
+    const int* wall_items;
     double* slots;              // [nitems][2] wall-momentum partial sums
     unsigned int* ticket;       // CTA arrival counter of the launch (zero between launches)
 };

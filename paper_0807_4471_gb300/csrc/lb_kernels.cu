@@ -485,15 +485,7 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
     const int t_lx = tid % L::RX, t_j = tid / L::RX;
     static_assert(L::NT == L::RX * L::TY && L::TY >= 4, "one window cell per thread and row");
     auto slot = [&](int pos) { return reinterpret_cast<T2*>(smem + (pos % L::NB) * L::SLOT_BYTES); };
-    // descriptor of the lattice that owns work item it (descriptors sorted by item0)
-    auto find = [&](int it) {
-        int lo = 0, hi = a.nlat - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (a.lat[mid].item0 <= it) lo = mid; else hi = mid - 1;
-        }
-        return &a.lat[lo];
-    };
+    const int it_end = a.cta_items[blockIdx.x + 1];
 
     if (tid == 0) {
         s_fail = 0;
@@ -505,21 +497,21 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
     // Producer (thread 0): the blocks of this CTA's items, in order.  Item
     // tiles [ty_a, ty_b) need blocks ty_a .. ty_b (block j = padded rows
     // [8j, 8j + 8)); consecutive items' blocks follow each other.
-    int p_item = blockIdx.x, p_j = 0, p_pos = 0;
+    int p_item = a.cta_items[blockIdx.x], p_j = 0, p_pos = 0;
     // cached geometry of the producer's current item
     const CUtensorMap* p_map = nullptr;
     int p_x0 = 0, p_ty_a = 0, p_nblk = 0;
     auto p_load = [&]() {
-        if (p_item >= a.nitems) return;
-        const LatDesc<C>* d = find(p_item);
-        const int local = p_item - d->item0;
-        p_x0 = (local % d->nstrips) * L::TX;
-        p_ty_a = (local / d->nstrips) * d->seg;
-        p_nblk = min(p_ty_a + d->seg, d->ntiles_y) - p_ty_a + 1;
+        if (p_item >= it_end) return;
+        const int4 w = a.items[p_item];
+        const LatDesc<C>* d = &a.lat[w.x];
+        p_x0 = w.y * L::TX;
+        p_ty_a = w.z;
+        p_nblk = w.w - w.z + 1;
         p_map = &d->tin[*((volatile int*)&d->st->cur)];
     };
     auto issue_next = [&]() -> bool {
-        if (p_item >= a.nitems) return false;
+        if (p_item >= it_end) return false;
         uint64_t* bar = &bars[p_pos % L::NB];
         mbar_expect_tx(bar, (uint32_t)L::SLOT_BYTES);
         // box origin: pair column x0 (= x0 - gx + gx) -> element 2 x0; padded row 8j
@@ -527,7 +519,7 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
         ++p_pos;
         if (++p_j == p_nblk) {
             p_j = 0;
-            p_item += G;
+            ++p_item;
             p_load();
         }
         return true;
@@ -539,12 +531,12 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
     double red[4] = {0.0, 0.0, 0.0, 0.0};
     bool bad = false;
     int c_pos = 0;   // ring position of the current item's first block
-    for (int it = blockIdx.x; it < a.nitems && !s_fail; it += G) {
-        const LatDesc<C>* d = find(it);
-        const int local = it - d->item0;
-        const int x0 = (local % d->nstrips) * L::TX;
-        const int ty_a = (local / d->nstrips) * d->seg;
-        const int ty_b = min(ty_a + d->seg, d->ntiles_y);
+    for (int it = a.cta_items[blockIdx.x]; it < it_end && !s_fail; ++it) {
+        const int4 w = a.items[it];
+        const LatDesc<C>* d = &a.lat[w.x];
+        const int x0 = w.y * L::TX;
+        const int ty_a = w.z;
+        const int ty_b = w.w;
         const Geom g = d->g;
         const LatVals<C> v = d->v;
         const bool per = ALLPER || g.periodic;
@@ -706,13 +698,12 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
         DevStats* st = d->st;
         const long long t = st->t;
         if (!ALLPER && !d->g.periodic) {
-            const int n = d->nstrips * ((d->ntiles_y + d->seg - 1) / d->seg);
-            const volatile double* vs = a.slots + 2 * d->item0;
+            const int ns = d->nstrips;
+            const int* wi = a.wall_items + d->wall0;
+            const volatile double* vs = a.slots;
             double sb = 0.0, stp = 0.0;
-            for (int i = 0; i < n; ++i) {
-                sb += vs[2 * i];
-                stp += vs[2 * i + 1];
-            }
+            for (int i = 0; i < ns; ++i) sb += vs[2 * wi[i]];
+            for (int i = 0; i < ns; ++i) stp += vs[2 * wi[ns + i] + 1];
             const long long every = d->stress_every > 0 ? d->stress_every : 1;
             if (t >= d->stress_t0 && ((t - d->stress_t0) % every) == 0) {
                 st->sum_bot += sb / d->g.nx;

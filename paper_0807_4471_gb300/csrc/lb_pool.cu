@@ -21,7 +21,7 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int kGraphChunk = 16;   // steps per captured graph
-constexpr int kTuneSteps = 2;     // timed steps per candidate partition
+constexpr int kTuneSteps = 6;     // timed steps per candidate partition
 
 // First-fit allocator over [0, size) with kAlign granularity.
 class Arena {
@@ -138,8 +138,12 @@ lb_status build(lb_pool* P, int seg) {
     for (int j : P->active) lats.push_back(&P->members[(size_t)j].lat);
     const int nlat = (int)lats.size();
     // slots: 2 per item; items are largest for seg = 1 (one per tile)
-    size_t need = 0;
-    for (Lattice* L : lats) need += 2 * (size_t)L->nstrips * (size_t)L->ntiles_y;
+    size_t tiles = 0, strips = 0;
+    for (Lattice* L : lats) {
+        tiles += (size_t)L->nstrips * (size_t)L->ntiles_y;
+        strips += (size_t)L->nstrips;
+    }
+    const size_t need = launch_area_doubles(tiles, strips, P->sms);
     if (need > P->slot_cap) {
         cudaError_t e = cudaStreamSynchronize(P->stream);
         if (P->slots) cudaFree(P->slots);
@@ -211,7 +215,8 @@ long long tune(lb_pool* P, long long budget_steps, lb_status* st) {
         nt.push_back(L->ntiles_y);
         tiles = std::max(tiles, L->ntiles_y);
     }
-    std::vector<int> cand = {choose_seg(ns.data(), nt.data(), (int)lats.size(), P->sms)};
+    // contiguous runs per CTA, the load-balance model's segments, then fixed segments
+    std::vector<int> cand = {-1, choose_seg(ns.data(), nt.data(), (int)lats.size(), P->sms)};
     for (int c : {1, 2, 4, 8, 16, 32, 64})
         if (c <= tiles && std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
     if ((long long)cand.size() * kTuneSteps > budget_steps) return 0;

@@ -51,7 +51,7 @@ def test_pool_members_match_single_lattices(lb, prec):
         assert left == len(MEMBERS) - 1       # the 30-step member is done
         assert pool.poll(jobs[2][0]) == (30, True)
         assert pool.run(25) == 0
-        assert pool.segment >= 1
+        assert pool.segment != 0              # a partition was built (-1: contiguous runs)
         for j, m, steps, seed in jobs:
             assert pool.poll(j) == (steps, True)
             got = pool.fields(j)
