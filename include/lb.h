@@ -243,6 +243,12 @@ lb_status lb_pool_run(lb_pool* pool, int64_t quantum, int32_t* active);
 /* Steps done and whether the member has finished (all its steps). */
 lb_status lb_pool_poll(lb_pool* pool, lb_job job, int64_t* steps_done, int32_t* done);
 
+/* As lb_init_fields for one member: restart it from caller FP64 host fields
+ * (rho_A, rho_B required; ux, uy may be NULL for rest) at step 0, with its
+ * scheduled step count unchanged and none of it done. */
+lb_status lb_pool_init_fields(lb_pool* pool, lb_job job, const double* rho_A, const double* rho_B,
+                              const double* ux, const double* uy);
+
 /* As lb_fields / lb_stress for one member (synchronise the pool stream). */
 lb_status lb_pool_fields(lb_pool* pool, lb_job job, double* rho_A, double* rho_B, double* ux,
                          double* uy);

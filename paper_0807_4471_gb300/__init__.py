@@ -104,6 +104,7 @@ def load():
             "lb_pool_run": (C.c_int, [H, C.c_int64, C.POINTER(C.c_int32)]),
             "lb_pool_poll": (C.c_int, [H, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
             "lb_pool_fields": (C.c_int, [H, C.c_int32, dp, dp, dp, dp]),
+            "lb_pool_init_fields": (C.c_int, [H, C.c_int32, dp, dp, dp, dp]),
             "lb_pool_stress": (C.c_int, [H, C.c_int32, C.POINTER(lb_stress_out)]),
             "lb_pool_release": (C.c_int, [H, C.c_int32]),
             "lb_pool_segment": (C.c_int32, [H]),
@@ -250,6 +251,11 @@ def lb_pool_poll(pool: int, job: int):
 def lb_pool_fields(pool: int, job: int, rho_A=None, rho_B=None, ux=None, uy=None):
     _check(load().lb_pool_fields(C.c_void_p(pool), job, _dp(rho_A), _dp(rho_B), _dp(ux),
                                  _dp(uy)), "lb_pool_fields")
+
+
+def lb_pool_init_fields(pool: int, job: int, rho_A, rho_B, ux=None, uy=None):
+    _check(load().lb_pool_init_fields(C.c_void_p(pool), job, _dp(rho_A), _dp(rho_B), _dp(ux),
+                                      _dp(uy)), "lb_pool_init_fields")
 
 
 def lb_pool_stress(pool: int, job: int) -> dict:
@@ -413,6 +419,10 @@ class Pool:
         out = [np.empty((ny, nx)) for _ in range(4)]
         lb_pool_fields(self.h, job, *out)
         return out
+
+    def init_fields(self, job: int, rho_A, rho_B, ux=None, uy=None):
+        """Restart member `job` from FP64 host fields (C-contiguous, ny x nx)."""
+        lb_pool_init_fields(self.h, job, rho_A, rho_B, ux, uy)
 
     def stress(self, job: int) -> dict:
         return lb_pool_stress(self.h, job)

@@ -404,6 +404,17 @@ lb_status lb_pool_fields(lb_pool* P, lb_job job, double* rho_A, double* rho_B, d
     return lattice_fields(P->members[(size_t)job].lat, rho_A, rho_B, ux, uy, P->stream);
 }
 
+lb_status lb_pool_init_fields(lb_pool* P, lb_job job, const double* rho_A, const double* rho_B,
+                              const double* ux, const double* uy) {
+    if (!P || !rho_A || !rho_B || job < 0 || (size_t)job >= P->members.size() ||
+        !P->members[(size_t)job].used)
+        return LB_ERR_INVALID;
+    Member& m = P->members[(size_t)job];
+    lb_status s = lattice_init_fields(m.lat, rho_A, rho_B, ux, uy, P->stream);
+    if (s == LB_OK) m.done = 0;   // the member restarts from these fields
+    return s;
+}
+
 lb_status lb_pool_stress(lb_pool* P, lb_job job, lb_stress_out* out) {
     if (!P || !out || job < 0 || (size_t)job >= P->members.size() || !P->members[(size_t)job].used)
         return LB_ERR_INVALID;

@@ -84,3 +84,29 @@ def test_pool_admission_by_footprint(lb):
         with pytest.raises(lb.LbError) as e:
             pool.admit(bad, 6, 10)             # couplings differ from the pool's
         assert e.value.status == lb.LB_ERR_INVALID
+
+
+def test_pool_init_fields_matches_handle(lb):
+    """lb_pool_init_fields restarts a member from host fields: the member then
+    steps bitwise like a handle initialised with lb_init_fields."""
+    m = model(120, 48, boundary=1, u_wall=0.01)
+    p = gpu_params(lb, m, "fp32")
+    rng = np.random.default_rng(21)
+    ra = np.ascontiguousarray(0.7 * (1 + 0.03 * (2 * rng.random((48, 120)) - 1)))
+    rb = np.ascontiguousarray(0.7 * (1 + 0.03 * (2 * rng.random((48, 120)) - 1)))
+    g = lb.Lattice(p).init_fields(ra, rb)
+    g.step(17)
+    want = g.fields()
+    g.close()
+    with lb.Pool(p, 4 * lb.Pool.footprint(p), max_jobs=2) as pool:
+        j = pool.admit(p, 5, 17)
+        other = pool.admit(p, 6, 40)
+        pool.run(3)                     # the member's seeded start is discarded
+        pool.init_fields(j, ra, rb)
+        assert pool.poll(j) == (0, False)
+        pool.run(17)
+        assert pool.poll(j) == (17, True)
+        got = pool.fields(j)
+        for a, b in zip(got, want):
+            assert np.array_equal(a, b)
+        assert pool.poll(other)[0] == 20
