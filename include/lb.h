@@ -262,6 +262,11 @@ lb_status lb_pool_release(lb_pool* pool, lb_job job);
  * CTA; 0 if none is built. */
 int32_t lb_pool_segment(const lb_pool* pool);
 
+/* Fix the work partition instead of measuring candidates: seg > 0 segments
+ * of seg tiles dealt to the CTAs in turn, -1 one contiguous run of tiles per
+ * CTA, 0 back to autotuning.  Applies from the next lb_pool_run. */
+lb_status lb_pool_set_partition(lb_pool* pool, int32_t seg);
+
 lb_status lb_pool_destroy(lb_pool* pool);
 
 /* Largest lattice, nx * ny, that lb_totals_noalloc accepts (4096 x 4096). */

@@ -108,6 +108,7 @@ def load():
             "lb_pool_stress": (C.c_int, [H, C.c_int32, C.POINTER(lb_stress_out)]),
             "lb_pool_release": (C.c_int, [H, C.c_int32]),
             "lb_pool_segment": (C.c_int32, [H]),
+            "lb_pool_set_partition": (C.c_int, [H, C.c_int32]),
             "lb_pool_destroy": (C.c_int, [H]),
         }
         for name, (res, args) in sig.items():
@@ -272,6 +273,10 @@ def lb_pool_segment(pool: int) -> int:
     return load().lb_pool_segment(C.c_void_p(pool))
 
 
+def lb_pool_set_partition(pool: int, seg: int):
+    _check(load().lb_pool_set_partition(C.c_void_p(pool), seg), "lb_pool_set_partition")
+
+
 def lb_pool_destroy(pool: int):
     _check(load().lb_pool_destroy(C.c_void_p(pool)), "lb_pool_destroy")
 
@@ -434,6 +439,10 @@ class Pool:
     @property
     def segment(self) -> int:
         return lb_pool_segment(self.h)
+
+    def set_partition(self, seg: int):
+        """Fix the work partition (seg > 0 segments, -1 contiguous runs, 0 autotune)."""
+        lb_pool_set_partition(self.h, seg)
 
     def close(self):
         if getattr(self, "h", None):

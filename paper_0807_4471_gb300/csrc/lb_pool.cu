@@ -82,6 +82,7 @@ struct Member {
 
 struct lb_pool {
     lb_params shared;
+    int forced_seg;          // 0: autotune; else the partition to use (-1: contiguous runs)
     cudaStream_t stream;
     bool own_stream;
     int device, sms;
@@ -361,7 +362,9 @@ lb_status lb_pool_run(lb_pool* P, int64_t quantum, int32_t* active_out) {
         if (!P->built || act != P->active) {
             P->active = act;
             auto it = P->tuned.find(signature(P));
-            if (it != P->tuned.end()) {
+            if (P->forced_seg != 0) {
+                s = build(P, P->forced_seg);
+            } else if (it != P->tuned.end()) {
                 s = build(P, it->second);
             } else {
                 const long long used = tune(P, k, &s);
@@ -437,6 +440,13 @@ lb_status lb_pool_release(lb_pool* P, lb_job job) {
 }
 
 int32_t lb_pool_segment(const lb_pool* P) { return P && P->built ? P->launch.seg : 0; }
+
+lb_status lb_pool_set_partition(lb_pool* P, int32_t seg) {
+    if (!P || seg < -1) return LB_ERR_INVALID;
+    P->forced_seg = seg;
+    P->built = false;   // rebuilt with it before the next step
+    return LB_OK;
+}
 
 lb_status lb_pool_destroy(lb_pool* P) {
     if (!P) return LB_OK;

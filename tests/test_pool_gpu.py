@@ -110,3 +110,32 @@ def test_pool_init_fields_matches_handle(lb):
         for a, b in zip(got, want):
             assert np.array_equal(a, b)
         assert pool.poll(other)[0] == 20
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_pool_tuned_partitions_match_single_lattices(lb, prec):
+    """A run long enough for the autotuner to time every candidate partition
+    (dealt segments, contiguous runs) on the real steps, then a forced
+    contiguous partition, still gives bitwise the single-lattice result: the
+    per-site arithmetic and the wall-sum order do not depend on the
+    partition."""
+    members = [dict(nx=200, ny=136), dict(nx=96, ny=64, boundary=1, u_wall=0.02, init_shear=1),
+               dict(nx=128, ny=128, rho0=0.55)]
+    steps = 150
+    shared = gpu_params(lb, model(64, 64), prec)
+    ps = [gpu_params(lb, model(**m), prec) for m in members]
+    budget = sum(lb.Pool.footprint(p) for p in ps) + (1 << 20)
+    with lb.Pool(shared, budget, max_jobs=len(members)) as pool:
+        jobs = [pool.admit(p, 11 + k, steps) for k, p in enumerate(ps)]
+        assert pool.run(steps - 20) == len(members)
+        assert pool.segment != 0
+        pool.set_partition(-1)
+        assert pool.run(20) == 0
+        assert pool.segment == -1
+        for k, (j, m) in enumerate(zip(jobs, members)):
+            want, st_single = _single(lb, model(**m), prec, 11 + k, steps)
+            for a, b in zip(pool.fields(j), want):
+                assert np.array_equal(a, b)
+            st = pool.stress(j)
+            for key in ("sigma_bot", "sigma_top", "samples", "step"):
+                assert st[key] == st_single[key], key
