@@ -298,6 +298,14 @@ lb_status lb_pool_destroy(lb_pool* pool);
 lb_status lb_totals_noalloc(int32_t nx, int32_t ny, const double* rho_A, const double* rho_B,
                             const double* ux, const double* uy, double* totals, void* stream);
 
+/* Diagnostic, no counterpart in the paper: runs the step kernel's bounded
+ * mbarrier wait on a barrier that nothing will complete, with a bound of
+ * `limit` polls (>= 1), on `stream`.  The wait gives up and the kernel
+ * latches its timeout flag, which comes back as LB_ERR_TIMEOUT; the context
+ * stays usable.  Any other status means the wait or the error path is
+ * broken.  Allocates (and frees) one word of device memory. */
+lb_status lb_selftest_wait(void* stream, int32_t limit);
+
 /* Static description of a status code. */
 const char* lb_status_string(lb_status s);
 

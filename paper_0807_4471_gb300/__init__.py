@@ -108,6 +108,7 @@ def load():
             "lb_pool_stress": (C.c_int, [H, C.c_int32, C.POINTER(lb_stress_out)]),
             "lb_pool_release": (C.c_int, [H, C.c_int32]),
             "lb_pool_segment": (C.c_int32, [H]),
+            "lb_selftest_wait": (C.c_int, [H, C.c_int32]),
             "lb_pool_set_partition": (C.c_int, [H, C.c_int32]),
             "lb_pool_destroy": (C.c_int, [H]),
         }
@@ -267,6 +268,11 @@ def lb_pool_stress(pool: int, job: int) -> dict:
 
 def lb_pool_release(pool: int, job: int):
     _check(load().lb_pool_release(C.c_void_p(pool), job), "lb_pool_release")
+
+
+def lb_selftest_wait(limit: int = 1024, stream: int = 0) -> int:
+    """Status of the bounded-wait self-test (LB_ERR_TIMEOUT when it works)."""
+    return load().lb_selftest_wait(C.c_void_p(stream), limit)
 
 
 def lb_pool_segment(pool: int) -> int:

@@ -5,6 +5,8 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lb_engine.h"
 
 using namespace lbgb;
@@ -168,12 +170,14 @@ lb_status lb_restore(lb_handle* h, const double* state, int64_t t, int32_t pulle
 lb_status lb_step(lb_handle* h, int64_t n) {
     if (!h || n < 0) return LB_ERR_INVALID;
     if (!h->lat.inited) return LB_ERR_STATE;
-    for (int64_t k = 0; k < n; ++k) {
-        lb_status s = launch_run(h->launch, h->stream);
-        if (s != LB_OK) return s;
-        lattice_advanced(h->lat, 1);
+    nvtxRangePushA("lb_step");   // a profiler range around the launches (free without a tool)
+    lb_status s = LB_OK;
+    for (int64_t k = 0; k < n && s == LB_OK; ++k) {
+        s = launch_run(h->launch, h->stream);
+        if (s == LB_OK) lattice_advanced(h->lat, 1);
     }
-    return LB_OK;
+    nvtxRangePop();
+    return s;
 }
 
 lb_status lb_fields(lb_handle* h, double* rho_A, double* rho_B, double* ux, double* uy) {
@@ -211,6 +215,25 @@ lb_status lb_destroy(lb_handle* h) {
     }
     delete h;
     return cuda_status(e);
+}
+
+lb_status lb_selftest_wait(void* stream, int32_t limit) {
+    if (limit < 1) return LB_ERR_INVALID;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned int* err = nullptr;
+    cudaError_t e = cudaMalloc(&err, sizeof(unsigned int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? LB_ERR_NOMEM : LB_ERR_CUDA;
+    }
+    unsigned int h = 0;
+    e = cudaMemsetAsync(err, 0, sizeof(unsigned int), s);
+    if (e == cudaSuccess) e = launch_wait_selftest(err, limit, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(err);
+    if (e != cudaSuccess) return cuda_status(e);
+    return (h & ERR_TIMEOUT) ? LB_ERR_TIMEOUT : LB_OK;
 }
 
 const char* lb_status_string(lb_status s) {

@@ -29,6 +29,9 @@ static_assert(sizeof(DevStats) == 128, "DevStats is one 128-byte line");
 
 enum : unsigned int { ERR_NONFINITE = 1u, ERR_TIMEOUT = 2u };
 
+// The bounded-wait self-test kernel (lb_selftest_wait).
+cudaError_t launch_wait_selftest(unsigned int* err, int limit, cudaStream_t s);
+
 // Geometry of the ghost-padded population planes.  Plane i (i = 0..8, the
 // D2Q9 direction) holds (ny + 2*kGY) rows of `pitch` interleaved (A, B)
 // pairs; lattice site (x, y) sits at row y + kGY, pair column x + gx.  The

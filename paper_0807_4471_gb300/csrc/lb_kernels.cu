@@ -88,9 +88,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 // Bounded wait: each try_wait suspends for a hardware-chosen interval, so the
-// bound is a few seconds at most.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (int it = 0; it < (1 << 22); ++it)
+// default bound is a few seconds at most.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  int limit = 1 << 22) {
+    for (int it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -911,6 +912,23 @@ __global__ void k_load_pops(Geom g, typename Prec<P>::C rho_ref, typename Prec<P
     }
 }
 
+// ------------------------------------------------------ wait self-test
+// One CTA arms an mbarrier that no copy will ever complete and waits on it
+// with the step kernel's bounded wait (bound `limit`); the wait gives up, the
+// kernel latches ERR_TIMEOUT in *err and returns, leaving the context usable.
+// (Compiled in the FP32 translation unit only.)
+#if LB_PREC == 1
+__global__ void k_wait_selftest(unsigned int* err, int limit) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0, limit)) atomicOr(err, ERR_TIMEOUT);
+}
+#endif
+
 // ------------------------------------------------------------- launchers
 template <int P, typename KS, typename KO>
 static cudaError_t configure(KS ks, KO ko) {
@@ -1015,3 +1033,12 @@ template cudaError_t launch_init_prec<LB_PREC>(const Geom&, const void*, void*, 
                                                cudaStream_t);
 
 }  // namespace lbgb
+
+#if LB_PREC == 1
+namespace lbgb {
+cudaError_t launch_wait_selftest(unsigned int* err, int limit, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(err, limit);
+    return cudaGetLastError();
+}
+}  // namespace lbgb
+#endif

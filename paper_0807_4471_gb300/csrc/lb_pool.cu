@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lb_engine.h"
 
 using namespace lbgb;
@@ -346,6 +348,10 @@ lb_status lb_pool_admit(lb_pool* P, const lb_params* p, uint64_t seed, int64_t s
 
 lb_status lb_pool_run(lb_pool* P, int64_t quantum, int32_t* active_out) {
     if (!P || quantum < 0) return LB_ERR_INVALID;
+    struct Range {   // a profiler range around the quantum (free without a tool)
+        Range() { nvtxRangePushA("lb_pool_run"); }
+        ~Range() { nvtxRangePop(); }
+    } range;
     long long remaining = quantum;
     lb_status s = LB_OK;
     while (remaining > 0) {

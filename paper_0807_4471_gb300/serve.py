@@ -16,6 +16,7 @@ library's kernels.
 from __future__ import annotations
 
 import collections
+import json
 import time
 from dataclasses import dataclass, field
 from typing import Callable, Optional
@@ -50,6 +51,7 @@ class Stats:
     finished: int = 0
     failed: int = 0
     refused_nomem: int = 0
+    cancelled: int = 0
     site_updates: int = 0
     quanta: int = 0
 
@@ -63,17 +65,20 @@ class Server:
     turns a job spec into the library's ``lb_params``.  Queued jobs are
     admitted in arrival order; a later, smaller job may go ahead of one that
     does not fit yet (backfill) unless the head of the queue has waited more
-    than `max_bypass` quanta."""
+    than `max_bypass` quanta.  With `log_path`, every job that ends
+    (finished, failed or cancelled) appends one JSON line: id, spec,
+    arrival / admission / end times, latency, steps and result or error."""
 
     def __init__(self, pool, make_params: Callable[[dict], object], quantum: int = 100,
                  keep_fields: bool = False, max_bypass: int = 20,
-                 clock: Callable[[], float] = time.perf_counter):
+                 clock: Callable[[], float] = time.perf_counter, log_path: Optional[str] = None):
         self.pool = pool
         self.make_params = make_params
         self.quantum = int(quantum)
         self.keep_fields = keep_fields
         self.max_bypass = max_bypass
         self.clock = clock
+        self.log_path = log_path
         self.queue: collections.deque[Job] = collections.deque()
         self.running: dict[int, Job] = {}
         self.done: list[Job] = []
@@ -88,6 +93,36 @@ class Server:
         self._next_id += 1
         self.queue.append(job)
         return job
+
+    def cancel(self, job: Job) -> bool:
+        """Withdraw a queued job, or stop a running one and free its memory
+        (between quanta: no kernel of the pool is in flight then).  Returns
+        False if the job had already ended."""
+        if job.done:
+            return False
+        if job in self.queue:
+            self.queue.remove(job)
+        elif job._slot in self.running and self.running[job._slot] is job:
+            self.pool.release(job._slot)
+            del self.running[job._slot]
+        else:
+            return False
+        job.error = "cancelled"
+        job.finished = self.clock()
+        self.done.append(job)
+        self.stats.cancelled += 1
+        self._log(job)
+        return True
+
+    def _log(self, job: Job):
+        if not self.log_path:
+            return
+        rec = dict(id=job.id, spec=job.spec, arrival=job.arrival, admitted=job.admitted,
+                   finished=job.finished, latency=job.latency, error=job.error,
+                   result=None if job.result is None else
+                   {k: v for k, v in job.result.items() if k != "fields"})
+        with open(self.log_path, "a") as fh:
+            fh.write(json.dumps(rec) + "\n")
 
     # ------------------------------------------------------------ serving
     def _admit(self):
@@ -112,6 +147,7 @@ class Server:
                 self.queue.remove(job)
                 self.done.append(job)
                 self.stats.failed += 1
+                self._log(job)
                 continue
             job.admitted = self.clock()
             self.queue.remove(job)
@@ -143,6 +179,7 @@ class Server:
             self.done.append(job)
             self.stats.finished += 1
             self.stats.site_updates += int(job.spec["nx"]) * int(job.spec["ny"]) * steps
+            self._log(job)
 
     def step(self) -> int:
         """One scheduling round.  Returns the number of resident jobs."""

@@ -103,3 +103,30 @@ def test_percentile():
     from paper_0807_4471_gb300.serve import percentile
     assert percentile([1, 2, 3, 4, 5], 50) == 3
     assert percentile(range(101), 99) == 99
+
+
+def test_cancel_queued_and_running_jobs_and_log(lb, tmp_path):
+    """A queued job is withdrawn, a running one is stopped and its memory
+    freed for the next admission; each ended job leaves one JSON line."""
+    import json
+    from paper_0807_4471_gb300.serve import Server
+    pool = FakePool(budget=2 * 64 * 64, lb=lb)
+    log = tmp_path / "jobs.jsonl"
+    srv = Server(pool, make, quantum=10, log_path=str(log))
+    a = srv.submit(dict(nx=64, ny=64, steps=1000))
+    b = srv.submit(dict(nx=64, ny=64, steps=30))
+    c = srv.submit(dict(nx=64, ny=64, steps=20))      # does not fit yet
+    srv.step()
+    assert a._slot in srv.running and b._slot in srv.running and c in srv.queue
+    assert srv.cancel(a)                              # running: memory freed
+    assert pool.used == 64 * 64
+    d = srv.submit(dict(nx=64, ny=64, steps=10))
+    assert srv.cancel(d)                              # queued: withdrawn
+    assert not srv.cancel(d)
+    srv.run_until_idle()
+    assert b.result and c.result and a.error == "cancelled" and d.error == "cancelled"
+    assert srv.stats.cancelled == 2 and srv.stats.finished == 2
+    recs = [json.loads(line) for line in log.read_text().splitlines()]
+    assert sorted(r["id"] for r in recs) == sorted([a.id, b.id, c.id, d.id])
+    assert {r["id"]: r["error"] for r in recs}[a.id] == "cancelled"
+    assert all(r["latency"] is not None for r in recs)
