@@ -216,16 +216,17 @@ def peak_lattice(torch, lb, precision: str, n: int, steps: int):
     return mlups, mlups * 1e6 * BYTES_PER_SITE[precision] / 1e9
 
 
-def batched_mix(torch, lb, steps: int):
+def batched_mix(torch, lb, steps: int, precision: str = "fp16"):
     """The batched workload: 64 lattices (sizes from {128, 256, 512, 1024}^2,
-    rho0 in [0.55, 0.83], half Couette), FP16 offsets, one pool launch per
-    step.  Aggregate MLUPS over `steps` steps after a tuning warm-up."""
+    rho0 in [0.55, 0.83], half Couette), FP16 offsets (or `precision`), one
+    pool launch per step.  Aggregate MLUPS over `steps` steps after a tuning
+    warm-up."""
     jobs = lbinputs.sample_batch()
     stream = torch.cuda.Stream()
-    shared = lb.make_params(128, 128, "fp16", psi_form=lb.LB_PSI_RHO0)
+    shared = lb.make_params(128, 128, precision, psi_form=lb.LB_PSI_RHO0)
     params = []
     for j in jobs:
-        params.append(lb.make_params(j["nx"], j["ny"], "fp16", psi_form=lb.LB_PSI_RHO0,
+        params.append(lb.make_params(j["nx"], j["ny"], precision, psi_form=lb.LB_PSI_RHO0,
                                      rho0=j["rho0"], boundary=j["boundary"],
                                      u_wall=lbinputs.wall_speed(j["shear_rate"], j["ny"]),
                                      init_shear=j["boundary"]))
@@ -246,15 +247,17 @@ def batched_mix(torch, lb, steps: int):
         sites = sum(p.nx * p.ny for p in params)
         return {"MLUPS": sites * steps / dt / 1e6, "lattices": len(params), "sites": sites,
                 "steps": steps, "segment": pool.segment, "ms_per_step": dt / steps * 1e3,
-                "GB_per_s_alg": sites * steps * 72 / dt / 1e9}
+                "GB_per_s_alg": sites * steps * BYTES_PER_SITE[precision] / dt / 1e9}
 
 
-def serving(torch, lb, njobs: int, step_scale: float, load: float, capacity_mlups: float):
+def serving(torch, lb, njobs: int, step_scale: float, load: float, capacity_mlups: float,
+            precision: str = "fp16"):
     """The served workload: the first `njobs` requests of the seeded arrival
     stream (square lattices 64..2048, rho0 in [0.55, 0.83], shear rate 0 or
     one of the 8 Couette rates), step counts scaled by `step_scale`, Poisson
-    arrivals at `load` x the measured batched capacity.  Jobs are served by
-    the continuous-batching server over a lattice pool (FP16 offsets)."""
+    arrivals at `load` x `capacity_mlups`.  Jobs are served by the
+    continuous-batching server over a lattice pool (FP16 offsets, or
+    `precision`)."""
     from paper_0807_4471_gb300.serve import Server, job_params, percentile
     specs = lbinputs.sample_serving()[:njobs]
     for sp in specs:
@@ -262,7 +265,7 @@ def serving(torch, lb, njobs: int, step_scale: float, load: float, capacity_mlup
     work = np.mean([sp["nx"] * sp["ny"] * sp["steps"] for sp in specs])
     gap = work / (load * capacity_mlups * 1e6)          # mean inter-arrival time (s)
     stream = [(sp["arrival"] * gap, sp) for sp in specs]
-    make = job_params(lb, dict(psi_form=lb.LB_PSI_RHO0), "fp16")
+    make = job_params(lb, dict(psi_form=lb.LB_PSI_RHO0), precision)
     cuda_stream = torch.cuda.Stream()
     budget = 48 << 30
     pool = lb.Pool(make(dict(nx=64, ny=64)), budget, max_jobs=1024, stream=cuda_stream)
@@ -275,7 +278,7 @@ def serving(torch, lb, njobs: int, step_scale: float, load: float, capacity_mlup
     return {"jobs": len(jobs), "failed": sum(1 for j in jobs if j.error), "p50_s": percentile(lat, 50),
             "p99_s": percentile(lat, 99), "MLUPS": srv.stats.site_updates / makespan / 1e6,
             "makespan_s": makespan, "step_scale": step_scale, "load": load,
-            "mean_interarrival_s": gap, "quantum": srv.quantum,
+            "mean_interarrival_s": gap, "quantum": srv.quantum, "precision": precision,
             "refused_nomem": srv.stats.refused_nomem}
 
 
@@ -403,9 +406,12 @@ def main():
             extra[f"peak_{p}_4096"] = {"MLUPS": mlups, "GB_per_s_alg": gbs,
                                        "frac_hbm": gbs / hbm_peak}
         extra["batched_64_fp16"] = batched_mix(torch, lb, 40)
+        extra["batched_64_fp32"] = batched_mix(torch, lb, 40, "fp32")
         if not args.no_serve:
-            extra["serving"] = serving(torch, lb, 300, 0.01, 0.8,
-                                       extra["batched_64_fp16"]["MLUPS"])
+            # the same arrival stream (rate set by the FP16 batched capacity) for both
+            cap = extra["batched_64_fp16"]["MLUPS"]
+            extra["serving"] = serving(torch, lb, 300, 0.01, 0.8, cap)
+            extra["serving_fp32"] = serving(torch, lb, 300, 0.01, 0.8, cap, "fp32")
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
