@@ -62,13 +62,13 @@ typedef enum {
 typedef enum { LB_FP64 = 0, LB_FP32 = 1, LB_FP16_OFFSET = 2, LB_BF16_OFFSET = 3 } lb_precision;
 
 /* Rounding of the half formats when a step stores its populations (FP32 and
- * FP64 always round to nearest).  LB_ROUND_STOCHASTIC rounds up with
- * probability equal to the fraction dropped, from a counter-based hash of
- * (site, step), so results stay reproducible and independent of how lattices
- * share a launch; round-to-nearest biases slow shear flows (the stored
- * non-equilibrium part is below one FP16 ulp near the walls), stochastic
- * rounding does not on average.  FP16 offsets below 2^-24 in magnitude keep
- * a bias below 2^-34. */
+ * FP64 always round to nearest).  LB_ROUND_STOCHASTIC rounds to one of the
+ * two neighbours with probability given by the distance to them (the
+ * hardware's stochastic-rounding conversion), with random bits from a
+ * counter-based hash of (site, step), so results stay reproducible and
+ * independent of how lattices share a launch; round-to-nearest biases slow
+ * shear flows (the stored non-equilibrium part is below one FP16 ulp near
+ * the walls), stochastic rounding does not on average. */
 typedef enum { LB_ROUND_NEAREST = 0, LB_ROUND_STOCHASTIC = 1 } lb_rounding;
 
 /* LB_COUETTE: x periodic, halfway bounce-back walls at y = -1/2 (velocity

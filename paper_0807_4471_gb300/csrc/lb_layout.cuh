@@ -82,24 +82,19 @@ template <> __device__ __forceinline__ __half2 enc2<__half2, float>(float a, flo
 template <> __device__ __forceinline__ __nv_bfloat162 enc2<__nv_bfloat162, float>(float a, float b) {
     return __floats2bfloat162_rn(a, b);
 }
-// Stochastic rounding of an FP32 pair to a 16-bit format: adding a uniform
-// random integer below 2^d to the bit pattern of |v| and truncating the d low
-// bits (round toward zero) rounds away from zero with probability equal to
-// the dropped fraction.  d = 13 for FP16 (exact for its normal range; below
-// 2^-14 more bits are dropped and the result leans toward zero by less than
-// one subnormal ulp), d = 16 for BF16.  r holds 32 random bits.
+// Stochastic rounding of an FP32 pair to a 16-bit format by the conversion
+// instruction of sm_100 and later (cvt.rs), which rounds each value to one of
+// its two neighbours with probability given by its distance to them, drawing
+// on the 32 random bits r.
 template <typename T2> __device__ __forceinline__ T2 enc2_sr(float2 v, uint32_t r);
 template <> __device__ __forceinline__ __half2 enc2_sr<__half2>(float2 v, uint32_t r) {
-    const float a = __uint_as_float(__float_as_uint(v.x) + (r >> 19));
-    const float b = __uint_as_float(__float_as_uint(v.y) + (r & 0x1fffu));
     uint32_t d;
-    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));   // high half = b
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(v.y), "f"(v.x), "r"(r));   // high half = y
     return *reinterpret_cast<const __half2*>(&d);
 }
 template <> __device__ __forceinline__ __nv_bfloat162 enc2_sr<__nv_bfloat162>(float2 v, uint32_t r) {
-    const uint32_t a = __float_as_uint(v.x) + (r >> 16);
-    const uint32_t b = __float_as_uint(v.y) + (r & 0xffffu);
-    const uint32_t d = __byte_perm(a, b, 0x7632);   // low half = a's high half, high half = b's
+    uint32_t d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(v.y), "f"(v.x), "r"(r));
     return *reinterpret_cast<const __nv_bfloat162*>(&d);
 }
 
