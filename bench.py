@@ -233,7 +233,7 @@ def batched_mix(torch, lb, steps: int, precision: str = "fp16"):
     budget = sum(lb.Pool.footprint(p) for p in params) + (64 << 20)
     with lb.Pool(shared, budget, max_jobs=len(params), stream=stream) as pool:
         ids = [pool.admit(p, j["seed"], 10 ** 6) for p, j in zip(params, jobs)]
-        pool.run(40)                     # tuning + warm-up
+        pool.run(100)                    # partition tuning (about 60 steps) + warm-up
         stream.synchronize()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)

@@ -301,7 +301,7 @@ struct Item {
 // seg > 0: segments of seg tiles, numbered lattice by lattice, segment row by
 // segment row, strip by strip; CTA b takes items b, b + G, ...
 // seg < 0: the tiles of all lattices in strip order (lattice, strip, tile
-// row) cut into G contiguous runs of equal length (+-1 tile), each run cut
+// row) cut into G contiguous runs of equal estimated cost, each run cut
 // again at strip boundaries: every CTA walks one or two strips.
 void partition(Lattice* const* lats, int nlat, int seg, int sms, std::vector<Item>& items,
                std::vector<int>& cta, int* grid) {
@@ -326,14 +326,49 @@ void partition(Lattice* const* lats, int nlat, int seg, int sms, std::vector<Ite
         return;
     }
     const int G = (int)std::min<long long>(tiles, sms);
-    long long pos = 0;   // global tile index of (l, sx, ty)
+    // Tile costs measured on GB300, relative to a full interior tile: tiles
+    // that write periodic ghost copies 1.26, ragged tiles 1.04, and the first
+    // tile of an item one tile more (its block ring fills and it computes 12
+    // deviation rows).  The runs cut the tile sequence at equal cumulative
+    // cost, counting an item start wherever a run begins or crosses a strip.
+    auto cost = [&](int l, int sx, int ty) {
+        const Lattice& L = *lats[l];
+        const int tx = kernel_tile_x(L.p.precision), tyy = kernel_tile_y(L.p.precision);
+        const int x0 = sx * tx, y0 = ty * tyy;
+        const bool full = x0 + tx <= L.p.nx && y0 + tyy <= L.p.ny;
+        if (!full) return 1.04;
+        const bool per = L.g.periodic != 0;
+        const bool edge = x0 < 3 || x0 + tx > L.p.nx - 3 || (per && (y0 < 3 || y0 + tyy > L.p.ny - 3));
+        return edge ? 1.26 : 1.0;
+    };
+    const double kItemStart = 1.0;
+    double total = 0.0;
+    for (int l = 0; l < nlat; ++l)
+        for (int sx = 0; sx < lats[l]->nstrips; ++sx) {
+            total += kItemStart;
+            for (int ty = 0; ty < lats[l]->ntiles_y; ++ty) total += cost(l, sx, ty);
+        }
+    total += kItemStart * G;   // roughly one extra item start per run
+    long long pos = 0;          // tiles assigned so far
     int l = 0, sx = 0, ty = 0;
+    double acc = 0.0;           // cumulative cost of the assigned tiles and item starts
     for (int b = 0; b < G; ++b) {
         cta.push_back((int)items.size());
-        long long end = tiles * (b + 1) / G;
-        while (pos < end) {
+        const double target = total * (b + 1) / G;
+        // at least one tile per run, and leave one tile for each later run
+        const long long max_end = tiles - (G - 1 - b);
+        const bool last = b == G - 1;
+        bool first = true;
+        while (pos < max_end && (first || acc < target || last)) {
+            // an item of at least one tile, then as many as the run's cost allows
             const int nt = lats[l]->ntiles_y;
-            const int take = (int)std::min<long long>(nt - ty, end - pos);
+            int take = 0;
+            acc += kItemStart;
+            do {
+                acc += cost(l, sx, ty + take);
+                ++take;
+            } while (ty + take < nt && pos + take < max_end && (acc < target || last));
+            first = false;
             items.push_back({l, sx, ty, ty + take});
             pos += take;
             ty += take;
@@ -376,7 +411,13 @@ lb_status launch_build(Launch& Ln, Lattice* const* lats, int nlat, void* descs, 
         tiles += (long long)lats[l]->nstrips * lats[l]->ntiles_y;
         strips += lats[l]->nstrips;
     }
-    const int seg = forced_seg != 0 ? forced_seg : choose_seg(ns.data(), nt.data(), nlat, sms);
+    // Default: cost-balanced contiguous runs while each CTA has up to ~40
+    // tiles (measured faster on 512^2-1024^2 lattices), the load-balance
+    // model's dealt segments beyond (their CTAs sweep a band of rows
+    // together, which keeps the halo columns in L2 on large lattices).
+    const int seg = forced_seg != 0 ? forced_seg
+                    : tiles <= 40LL * sms ? -1
+                                          : choose_seg(ns.data(), nt.data(), nlat, sms);
     std::vector<Item> items;
     std::vector<int> cta;
     int grid = 0;
