@@ -26,6 +26,7 @@
 #include <cuda_fp16.h>
 
 #include <cstdint>
+#include <cstdlib>
 
 #include "lb_internal.h"
 #include "lb_layout.cuh"
@@ -76,6 +77,14 @@ __device__ __forceinline__ void bulk_wait_read() {
 }
 // Wait until the committed bulk stores have completed.
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Programmatic dependent launch: wait for the grids this one depends on to
+// complete (their writes visible), and let this grid's dependents be
+// scheduled onto SMs as this grid's CTAs retire.  Both are no-ops when the
+// launch carries no programmatic dependency.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
@@ -376,6 +385,8 @@ __device__ __forceinline__ void site_update(
     if (o.stage != nullptr) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) o.stage[i * TY * TX] = e[i];
+        // staging writes before the bulk store, ahead of any global store
+        fence_proxy_async();
     }
     const int dX = !o.edge ? 0 : (x < 3) ? g.nx : ((x >= g.nx - 3) ? -g.nx : 0);
     long long dY = 0;
@@ -479,9 +490,13 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
     __shared__ __align__(8) uint64_t bars[L::NB];
     __shared__ int s_fail, s_last;
     __shared__ double s_red[L::NT / 32][4];
+    __shared__ int s_wany[L::NT / 32];
 
     const int tid = threadIdx.x;
     const int G = gridDim.x;
+    // thread 0 issues the block loads; this thread (warp 1) the bulk stores
+    // of the staging tile and the waits on them
+    constexpr int kStoreThread = 32;
     // window column and tile row of this thread (both phases)
     const int t_lx = tid % L::RX, t_j = tid / L::RX;
     static_assert(L::NT == L::RX * L::TY && L::TY >= 4, "one window cell per thread and row");
@@ -494,6 +509,12 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
         fence_mbar_init();
     }
     __syncthreads();
+    // Up to here only shared memory and the host-built item tables were
+    // touched; the lattice state (DevStats, populations) written by the
+    // previous step is read after the wait.  The next step's CTAs may then
+    // take each SM as soon as this CTA leaves it (one CTA fills an SM).
+    griddep_wait();
+    griddep_launch_dependents();
 
     // Producer (thread 0): the blocks of this CTA's items, in order.  Item
     // tiles [ty_a, ty_b) need blocks ty_a .. ty_b (block j = padded rows
@@ -529,7 +550,6 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
     if (tid == 0)
         while (p_pos < L::NB && issue_next()) {}
 
-    double red[4] = {0.0, 0.0, 0.0, 0.0};
     bool bad = false;
     int c_pos = 0;   // ring position of the current item's first block
     for (int it = a.cta_items[blockIdx.x]; it < it_end && !s_fail; ++it) {
@@ -597,7 +617,9 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
                     win_p[k * L::RX + t_lx] = p;
                 }
             }
-            if (!per) {   // mirror the deviations about the halfway walls
+            // mirror the deviations about the halfway walls, in the tiles whose
+            // window rows y0 - 2 .. y0 + TY + 1 reach past a wall (uniform)
+            if (!per && (y0 < 2 || y0 + L::TY + 1 >= g.ny)) {
                 __syncthreads();
                 for (int c = tid; c < L::WIN * L::RX; c += L::NT) {
                     const int k = c / L::RX, lx = c - k * L::RX;
@@ -611,7 +633,7 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
                     win_p[k * L::RX + lx] = win_p[km * L::RX + lx];
                 }
             }
-            if (tid == 0) bulk_wait_read();   // previous bulk store has read the staging tile
+            if (tid == kStoreThread) bulk_wait_read();   // previous bulk store has read the staging tile
             __syncthreads();
             if (s_fail) break;
 
@@ -643,18 +665,21 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
                     double wr[4] = {0.0, 0.0, 0.0, 0.0};
                     site_update<P, false, GEN, PS>(brow(ly + 2, bc), brow(ly + 3, bc), brow(ly + 4, bc),
                                                    ps, rr, x, y, per, pull, g, v, a.k, o, wr, bad);
-                    wall[0] += wr[0];
-                    wall[1] += wr[1];
-                    if (full) fence_proxy_async();   // staging writes before the bulk store
+                    if (!per && (y == 0 || y == g.ny - 1)) {   // FP64: wall rows only
+                        wall[0] += wr[0];
+                        wall[1] += wr[1];
+                    }
                 }
             }
             __syncthreads();
+            // The bulk store and the next loads are issued by two threads of
+            // different warps, side by side.
+            if (tid == kStoreThread && full) {
+                // site (x0, y0) in padded coordinates: pair column x0 + gx, row y0 + kGY
+                tma_store_3d(&d->tout[cur ^ 1], stage, 2 * (x0 + L::GX), y0 + kGY, 0);
+                bulk_commit();
+            }
             if (tid == 0) {
-                if (full) {
-                    // site (x0, y0) in padded coordinates: pair column x0 + gx, row y0 + kGY
-                    tma_store_3d(&d->tout[cur ^ 1], stage, 2 * (x0 + L::GX), y0 + kGY, 0);
-                    bulk_commit();
-                }
                 // blocks before the next tile's first block are free
                 const int released = (ty + 1 < ty_b) ? q + 1 : q + 2;
                 fence_proxy_async();   // generic reads of freed slots before async writes
@@ -667,18 +692,37 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
         }
         if (s_fail) break;
         c_pos += (ty_b - ty_a) + 1;
-        if (!per) {   // wall momentum of this item (zero unless it holds a wall row)
-            red[0] = wall[0];
-            red[1] = wall[1];
-            red[2] = red[3] = 0.0;
-            block_sum4<L::NT>(red, s_red);
+        if (!per && (ty_a == 0 || ty_b == d->ntiles_y)) {
+            // Wall momentum of an item holding a wall row (only these items'
+            // slots are read), in FP64.  FP64 issues at a small fraction of
+            // the FP32 rate, so only the warps that updated a wall site
+            // reduce, and thread 0 adds up just those warps, in warp order.
+            const int lane = tid & 31, warp = tid >> 5;
+            const bool mine = __any_sync(0xffffffffu, wall[0] != 0.0 || wall[1] != 0.0);
+            if (mine) {
+                wall[0] = warp_sum(wall[0]);
+                wall[1] = warp_sum(wall[1]);
+            }
+            __syncthreads();   // the previous item's reads of s_red are done
+            if (lane == 0) {
+                s_wany[warp] = mine ? 1 : 0;
+                s_red[warp][0] = wall[0];
+                s_red[warp][1] = wall[1];
+            }
+            __syncthreads();
             if (tid == 0) {
-                a.slots[2 * it] = red[0];
-                a.slots[2 * it + 1] = red[1];
+                double b = 0.0, t = 0.0;
+                for (int w = 0; w < L::NT / 32; ++w)
+                    if (s_wany[w]) {
+                        b += s_red[w][0];
+                        t += s_red[w][1];
+                    }
+                a.slots[2 * it] = b;
+                a.slots[2 * it + 1] = t;
             }
         }
     }
-    if (tid == 0) bulk_wait_all();
+    if (tid == kStoreThread) bulk_wait_all();
     if (s_fail && tid == 0) {
         // let copies in flight land before the CTA exits
         for (int b = 0; b < L::NB; ++b) mbar_wait_bounded(&bars[b], 0), mbar_wait_bounded(&bars[b], 1);
@@ -955,6 +999,16 @@ static cudaError_t ensure_configured() {
     return e;
 }
 
+// LB_PDL=0 in the environment turns the programmatic launches off (A/B
+// timing); read once per process.
+static bool pdl_enabled() {
+    static const bool on = [] {
+        const char* v = getenv("LB_PDL");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
 template <int P>
 cudaError_t launch_step_prec(const void* args, int variant, dim3 grid, cudaStream_t s) {
     typedef Layout<P> L;
@@ -962,13 +1016,26 @@ cudaError_t launch_step_prec(const void* args, int variant, dim3 grid, cudaStrea
     cudaError_t e = ensure_configured<P>();
     if (e != cudaSuccess) return e;
     const BatchArgs<C>& a = *reinterpret_cast<const BatchArgs<C>*>(args);
+    // Consecutive steps on a stream overlap the next launch's set-up with the
+    // previous launch's last CTAs (programmatic stream serialization); the
+    // kernel waits for the previous grid before it reads the lattice state.
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(L::NT, 1, 1);
+    cfg.dynamicSmemBytes = L::SMEM;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
     switch (variant & 3) {
-        case 0: k_step<P, 0><<<grid, L::NT, L::SMEM, s>>>(a); break;
-        case 1: k_step<P, 1><<<grid, L::NT, L::SMEM, s>>>(a); break;
-        case 2: k_step<P, 2><<<grid, L::NT, L::SMEM, s>>>(a); break;
-        default: k_step<P, 3><<<grid, L::NT, L::SMEM, s>>>(a); break;
+        case 0: e = cudaLaunchKernelEx(&cfg, k_step<P, 0>, a); break;
+        case 1: e = cudaLaunchKernelEx(&cfg, k_step<P, 1>, a); break;
+        case 2: e = cudaLaunchKernelEx(&cfg, k_step<P, 2>, a); break;
+        default: e = cudaLaunchKernelEx(&cfg, k_step<P, 3>, a); break;
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int P>
