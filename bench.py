@@ -233,7 +233,7 @@ def batched_mix(torch, lb, steps: int, precision: str = "fp16"):
     budget = sum(lb.Pool.footprint(p) for p in params) + (64 << 20)
     with lb.Pool(shared, budget, max_jobs=len(params), stream=stream) as pool:
         ids = [pool.admit(p, j["seed"], 10 ** 6) for p, j in zip(params, jobs)]
-        pool.run(100)                    # partition tuning (about 60 steps) + warm-up
+        pool.run(600)                    # partition tuning (about 60 steps) + warm-up
         stream.synchronize()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
@@ -269,7 +269,7 @@ def serving(torch, lb, njobs: int, step_scale: float, load: float, capacity_mlup
     cuda_stream = torch.cuda.Stream()
     budget = 48 << 30
     pool = lb.Pool(make(dict(nx=64, ny=64)), budget, max_jobs=1024, stream=cuda_stream)
-    srv = Server(pool, make, quantum=200)
+    srv = Server(pool, make, quantum=100)
     t0 = time.perf_counter()
     jobs = srv.replay(stream)
     makespan = time.perf_counter() - t0

@@ -216,7 +216,9 @@ lb_status lb_destroy(lb_handle* h);
  * consecutive steps over an unchanged member set are captured once into a
  * CUDA graph and replayed.  The work partition (segment length of the
  * column strips) is tuned by timing candidate partitions on the first steps
- * of each new member set (those steps are real steps) and cached.
+ * of each new member set (those steps are real steps) and cached; a member
+ * set that runs fewer than 8 times the steps the timing takes (about 400 to
+ * 500 steps) keeps the load-balance model's partition instead.
  * ------------------------------------------------------------------------ */
 typedef struct lb_pool lb_pool;
 typedef int32_t lb_job;

@@ -24,6 +24,10 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr int kGraphChunk = 16;   // steps per captured graph
 constexpr int kTuneSteps = 6;     // timed steps per candidate partition
+// A new member set is tuned only if it runs at least kTuneShare times the
+// steps that timing all candidates takes: a short-lived set (a server's
+// quantum between arrivals) keeps the load-balance model's partition.
+constexpr int kTuneShare = 8;
 
 // First-fit allocator over [0, size) with kAlign granularity.
 class Arena {
@@ -222,7 +226,7 @@ long long tune(lb_pool* P, long long budget_steps, lb_status* st) {
     std::vector<int> cand = {-1, choose_seg(ns.data(), nt.data(), (int)lats.size(), P->sms)};
     for (int c : {1, 2, 4, 8, 16, 32, 64})
         if (c <= tiles && std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
-    if ((long long)cand.size() * kTuneSteps > budget_steps) return 0;
+    if ((long long)cand.size() * kTuneSteps * kTuneShare > budget_steps) return 0;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);

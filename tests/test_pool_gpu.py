@@ -121,7 +121,7 @@ def test_pool_tuned_partitions_match_single_lattices(lb, prec):
     partition."""
     members = [dict(nx=200, ny=136), dict(nx=96, ny=64, boundary=1, u_wall=0.02, init_shear=1),
                dict(nx=128, ny=128, rho0=0.55)]
-    steps = 150
+    steps = 400                         # the member set runs long enough to be tuned
     shared = gpu_params(lb, model(64, 64), prec)
     ps = [gpu_params(lb, model(**m), prec) for m in members]
     budget = sum(lb.Pool.footprint(p) for p in ps) + (1 << 20)
