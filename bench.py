@@ -81,7 +81,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
@@ -285,7 +285,8 @@ def serving(torch, lb, njobs: int, step_scale: float, load: float, capacity_mlup
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 5000; the reference arm, a CPU oracle: 200)")
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=list(BYTES_PER_SITE))
@@ -298,6 +299,8 @@ def main():
     ap.add_argument("--lattices", type=int, default=len(lbinputs.CFG_SWEEP["rho0s"]),
                     help="number of sweep lattices stepped per bench step (profiling runs)")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 200 if args.impl == "reference" else 5000
     args.warmup = max(args.warmup, 3)
 
     if args.impl == "reference":
