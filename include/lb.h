@@ -271,6 +271,24 @@ lb_status lb_pool_set_partition(lb_pool* pool, int32_t seg);
 
 lb_status lb_pool_destroy(lb_pool* pool);
 
+/* Host only, no device work (usable without a GPU): the work items that one
+ * step launch over `nlat` lattices with parameters ps[0 .. nlat-1] would use
+ * on a device with `sms` SMs.  seg > 0: segments of seg tiles, each given in
+ * band order to the CTA with the least estimated work; -1: one cost-balanced
+ * contiguous run of tiles per CTA; 0: the library's default for these sizes.
+ * A tile is TX x TY sites (60 x 8; 28 x 8 for FP64), a strip a TX-wide
+ * column of tiles.  On entry *nitems is the capacity of `items` (in items of
+ * 4 int32: lattice index, strip, first tile row, end tile row) and *grid the
+ * capacity of `cta` (in entries); on return they hold the item count and the
+ * number of CTAs, items lists the items CTA by CTA, the items of CTA b are
+ * items[cta[b] .. cta[b + 1]) (grid + 1 entries), and *seg_used the
+ * partition applied.  LB_ERR_INVALID for an invalid lattice, mixed
+ * precisions, nlat or sms < 1, or a capacity too small (the sizes needed
+ * are still returned).  No pointer is retained. */
+lb_status lb_plan_partition(const lb_params* ps, int32_t nlat, int32_t seg, int32_t sms,
+                            int32_t* items, int32_t* nitems, int32_t* cta, int32_t* grid,
+                            int32_t* seg_used);
+
 /* Largest lattice, nx * ny, that lb_totals_noalloc accepts (4096 x 4096). */
 #define LB_NOALLOC_MAX_SITES 16777216
 

@@ -111,6 +111,9 @@ def load():
             "lb_selftest_wait": (C.c_int, [H, C.c_int32]),
             "lb_pool_set_partition": (C.c_int, [H, C.c_int32]),
             "lb_pool_destroy": (C.c_int, [H]),
+            "lb_plan_partition": (C.c_int, [C.POINTER(lb_params), C.c_int32, C.c_int32, C.c_int32,
+                                            C.c_void_p, C.POINTER(C.c_int32), C.c_void_p,
+                                            C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -285,6 +288,27 @@ def lb_pool_set_partition(pool: int, seg: int):
 
 def lb_pool_destroy(pool: int):
     _check(load().lb_pool_destroy(C.c_void_p(pool)), "lb_pool_destroy")
+
+
+def lb_plan_partition(params, seg: int = 0, sms: int = 152):
+    """Host-only work plan of one step launch over the lattices `params`:
+    (items int32[n, 4] = lattice, strip, first tile row, end tile row;
+    cta int32[grid + 1] offsets into items; the partition applied)."""
+    import numpy as np
+    L = load()
+    arr = (lb_params * len(params))(*params)
+    ni, ng, su = C.c_int32(0), C.c_int32(0), C.c_int32(0)
+    L.lb_plan_partition(arr, len(params), seg, sms, None, C.byref(ni), None, C.byref(ng),
+                        C.byref(su))
+    if ni.value < 1 or ng.value < 1:
+        raise LbError(LB_ERR_INVALID, "lb_plan_partition")
+    items = np.zeros((ni.value, 4), dtype=np.int32)
+    cta = np.zeros(ng.value + 1, dtype=np.int32)
+    ni.value, ng.value = items.shape[0], cta.shape[0]
+    _check(L.lb_plan_partition(arr, len(params), seg, sms, items.ctypes.data_as(C.c_void_p),
+                               C.byref(ni), cta.ctypes.data_as(C.c_void_p), C.byref(ng),
+                               C.byref(su)), "lb_plan_partition")
+    return items, cta, su.value
 
 
 LB_NOALLOC_MAX_SITES = 16777216

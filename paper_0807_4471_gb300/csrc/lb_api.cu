@@ -250,4 +250,10 @@ const char* lb_status_string(lb_status s) {
     return "unknown status";
 }
 
+lb_status lb_plan_partition(const lb_params* ps, int32_t nlat, int32_t seg, int32_t sms,
+                            int32_t* items, int32_t* nitems, int32_t* cta, int32_t* grid,
+                            int32_t* seg_used) {
+    return lbgb::plan_partition(ps, nlat, seg, sms, items, nitems, cta, grid, seg_used);
+}
+
 }  // extern "C"

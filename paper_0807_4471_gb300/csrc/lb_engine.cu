@@ -7,6 +7,9 @@
 
 #include <cmath>
 #include <cstring>
+#include <functional>
+#include <queue>
+#include <utility>
 
 namespace lbgb {
 
@@ -185,16 +188,19 @@ static EncodeTiledFn encode_fn() {
 
 // TMA descriptor of one population buffer: 9 direction planes of interleaved
 // (A, B) pairs, a row holding 2 * pitch elements.  Box: cols pairs x rows x
-// 9 planes.
+// 9 planes.  The descriptor spans the first ext_pairs pairs of each of the
+// first ext_rows rows (all of the padded plane when 0): a store clips what
+// falls outside.
 static lb_status make_tmap(CUtensorMap* m, int precision, const Geom& g, void* base, int cols,
-                           int rows) {
+                           int rows, int ext_pairs = 0, int ext_rows = 0) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return LB_ERR_CUDA;
     const int es = kernel_elem_bytes(precision);
     CUtensorMapDataType dt = precision == LB_FP64   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                              : precision == LB_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                                     : CU_TENSOR_MAP_DATA_TYPE_UINT16;
-    cuuint64_t dims[3] = {(cuuint64_t)(2 * g.pitch), (cuuint64_t)g.rows, 9};
+    cuuint64_t dims[3] = {(cuuint64_t)(2 * (ext_pairs > 0 ? ext_pairs : g.pitch)),
+                          (cuuint64_t)(ext_rows > 0 ? ext_rows : g.rows), 9};
     cuuint64_t strides[2] = {(cuuint64_t)(2 * g.pitch) * es,
                              (cuuint64_t)g.rows * (cuuint64_t)(2 * g.pitch) * es};
     cuuint32_t box[3] = {(cuuint32_t)(2 * cols), (cuuint32_t)rows, 9};
@@ -230,7 +236,11 @@ lb_status lattice_setup(Lattice& L, const lb_params* p, char* region) {
     lb_status s = LB_OK;
     for (int b = 0; b < 2 && s == LB_OK; ++b) {
         s = make_tmap(&L.tblock[b], p->precision, L.g, L.fbuf[b], bx, kernel_block_rows(p->precision));
-        if (s == LB_OK) s = make_tmap(&L.ttile[b], p->precision, L.g, L.fbuf[b], tx, ty);
+        // tile stores end at the lattice's last column and row: the ghost
+        // columns and rows beyond a ragged tile are never written by them
+        if (s == LB_OK)
+            s = make_tmap(&L.ttile[b], p->precision, L.g, L.fbuf[b], tx, ty, p->nx + L.g.gx,
+                          p->ny + kGY);
         if (s == LB_OK) s = make_tmap(&L.tobs[b], p->precision, L.g, L.fbuf[b], bx, ty + 2 * kGY);
     }
     return s;
@@ -309,28 +319,10 @@ void partition(Lattice* const* lats, int nlat, int seg, int sms, std::vector<Ite
     cta.clear();
     long long tiles = 0;
     for (int l = 0; l < nlat; ++l) tiles += (long long)lats[l]->nstrips * lats[l]->ntiles_y;
-    if (seg > 0) {
-        std::vector<Item> all;
-        for (int l = 0; l < nlat; ++l) {
-            const int ns = lats[l]->nstrips, nt = lats[l]->ntiles_y;
-            for (int a = 0; a < nt; a += seg)
-                for (int sx = 0; sx < ns; ++sx) all.push_back({l, sx, a, std::min(a + seg, nt)});
-        }
-        const int G = (int)std::min<long long>((long long)all.size(), sms);
-        for (int b = 0; b < G; ++b) {
-            cta.push_back((int)items.size());
-            for (size_t k = (size_t)b; k < all.size(); k += (size_t)G) items.push_back(all[k]);
-        }
-        cta.push_back((int)items.size());
-        *grid = G;
-        return;
-    }
-    const int G = (int)std::min<long long>(tiles, sms);
     // Tile costs measured on GB300, relative to a full interior tile: tiles
     // that write periodic ghost copies 1.26, ragged tiles 1.04, and the first
     // tile of an item one tile more (its block ring fills and it computes 12
-    // deviation rows).  The runs cut the tile sequence at equal cumulative
-    // cost, counting an item start wherever a run begins or crosses a strip.
+    // deviation rows).
     auto cost = [&](int l, int sx, int ty) {
         const Lattice& L = *lats[l];
         const int tx = kernel_tile_x(L.p.precision), tyy = kernel_tile_y(L.p.precision);
@@ -342,6 +334,41 @@ void partition(Lattice* const* lats, int nlat, int seg, int sms, std::vector<Ite
         return edge ? 1.26 : 1.0;
     };
     const double kItemStart = 1.0;
+    if (seg > 0) {
+        // Segments in band order (all strips of a segment row, row after row),
+        // each given to the CTA with the least work so far (the lowest index
+        // among equals): round-robin dealing when costs are equal, while the
+        // CTAs that draw the costlier edge segments take fewer of them.
+        std::vector<Item> all;
+        for (int l = 0; l < nlat; ++l) {
+            const int ns = lats[l]->nstrips, nt = lats[l]->ntiles_y;
+            for (int a = 0; a < nt; a += seg)
+                for (int sx = 0; sx < ns; ++sx) all.push_back({l, sx, a, std::min(a + seg, nt)});
+        }
+        const int G = (int)std::min<long long>((long long)all.size(), sms);
+        std::vector<std::vector<int>> mine((size_t)G);
+        typedef std::pair<double, int> Load;   // (work so far, CTA): smallest first
+        std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+        for (int b = 0; b < G; ++b) heap.push({0.0, b});
+        for (size_t k = 0; k < all.size(); ++k) {
+            const Load top = heap.top();
+            heap.pop();
+            double w = kItemStart;
+            for (int ty = all[k].ty_a; ty < all[k].ty_b; ++ty) w += cost(all[k].lat, all[k].strip, ty);
+            mine[(size_t)top.second].push_back((int)k);
+            heap.push({top.first + w, top.second});
+        }
+        for (int b = 0; b < G; ++b) {
+            cta.push_back((int)items.size());
+            for (int k : mine[(size_t)b]) items.push_back(all[(size_t)k]);
+        }
+        cta.push_back((int)items.size());
+        *grid = G;
+        return;
+    }
+    const int G = (int)std::min<long long>(tiles, sms);
+    // The runs cut the tile sequence at equal cumulative cost, counting an
+    // item start wherever a run begins or crosses a strip.
     double total = 0.0;
     for (int l = 0; l < nlat; ++l)
         for (int sx = 0; sx < lats[l]->nstrips; ++sx) {
@@ -387,6 +414,56 @@ void partition(Lattice* const* lats, int nlat, int seg, int sms, std::vector<Ite
 
 }  // namespace
 
+// Default partition: cost-balanced contiguous runs while each CTA has up to
+// ~40 tiles (measured faster on 512^2-1024^2 lattices), the load-balance
+// model's dealt segments beyond (their CTAs sweep a band of rows together,
+// which keeps the halo columns in L2 on large lattices).
+static int default_seg(long long tiles, const int* ns, const int* nt, int nlat, int sms) {
+    return tiles <= 40LL * sms ? -1 : choose_seg(ns, nt, nlat, sms);
+}
+
+// Host-only plan of a launch's work items (lb_plan_partition).
+lb_status plan_partition(const lb_params* ps, int nlat, int seg, int sms, int32_t* items,
+                         int32_t* nitems, int32_t* cta, int32_t* grid, int32_t* seg_used) {
+    if (!ps || nlat < 1 || sms < 1 || !nitems || !grid || !seg_used) return LB_ERR_INVALID;
+    std::vector<Lattice> lv((size_t)nlat);
+    std::vector<Lattice*> lp((size_t)nlat);
+    std::vector<int> ns((size_t)nlat), nt((size_t)nlat);
+    long long tiles = 0;
+    for (int l = 0; l < nlat; ++l) {
+        if (validate_params(&ps[l]) != LB_OK || ps[l].precision != ps[0].precision)
+            return LB_ERR_INVALID;
+        Lattice& L = lv[(size_t)l];
+        L.p = ps[l];
+        L.g = make_geom(&ps[l]);
+        const int tx = kernel_tile_x(ps[l].precision), ty = kernel_tile_y(ps[l].precision);
+        L.nstrips = (ps[l].nx + tx - 1) / tx;
+        L.ntiles_y = (ps[l].ny + ty - 1) / ty;
+        lp[(size_t)l] = &L;
+        ns[(size_t)l] = L.nstrips;
+        nt[(size_t)l] = L.ntiles_y;
+        tiles += (long long)L.nstrips * L.ntiles_y;
+    }
+    const int s = seg != 0 ? seg : default_seg(tiles, ns.data(), nt.data(), nlat, sms);
+    std::vector<Item> it;
+    std::vector<int> c;
+    int G = 0;
+    partition(lp.data(), nlat, s, sms, it, c, &G);
+    const int cap_items = *nitems, cap_cta = *grid;
+    *nitems = (int32_t)it.size();
+    *grid = G;
+    *seg_used = s;
+    if (cap_items < (int)it.size() || cap_cta < G + 1 || !items || !cta) return LB_ERR_INVALID;
+    for (size_t k = 0; k < it.size(); ++k) {
+        items[4 * k] = it[k].lat;
+        items[4 * k + 1] = it[k].strip;
+        items[4 * k + 2] = it[k].ty_a;
+        items[4 * k + 3] = it[k].ty_b;
+    }
+    for (int b = 0; b <= G; ++b) cta[b] = c[(size_t)b];
+    return LB_OK;
+}
+
 int launch_items(Lattice* const* lats, int nlat, int seg, int sms) {
     std::vector<Item> items;
     std::vector<int> cta;
@@ -411,13 +488,7 @@ lb_status launch_build(Launch& Ln, Lattice* const* lats, int nlat, void* descs, 
         tiles += (long long)lats[l]->nstrips * lats[l]->ntiles_y;
         strips += lats[l]->nstrips;
     }
-    // Default: cost-balanced contiguous runs while each CTA has up to ~40
-    // tiles (measured faster on 512^2-1024^2 lattices), the load-balance
-    // model's dealt segments beyond (their CTAs sweep a band of rows
-    // together, which keeps the halo columns in L2 on large lattices).
-    const int seg = forced_seg != 0 ? forced_seg
-                    : tiles <= 40LL * sms ? -1
-                                          : choose_seg(ns.data(), nt.data(), nlat, sms);
+    const int seg = forced_seg != 0 ? forced_seg : default_seg(tiles, ns.data(), nt.data(), nlat, sms);
     std::vector<Item> items;
     std::vector<int> cta;
     int grid = 0;

@@ -20,7 +20,7 @@ struct Lattice {
     char* fbuf[2];
     size_t fbytes;
     CUtensorMap tblock[2];   // step kernel: 8-row block loads of buffer b
-    CUtensorMap ttile[2];    // step kernel: full-tile stores into buffer b
+    CUtensorMap ttile[2];    // step kernel: tile stores into buffer b, clipped at the lattice edge
     CUtensorMap tobs[2];     // observe kernel: tile + halo loads of buffer b
     Coef<double> kd;
     Coef<float> kf;
@@ -49,6 +49,10 @@ int device_sms(int device);
 // Bytes of a lattice's device region, and binding a lattice to one.
 size_t lattice_bytes(const lb_params* p);
 lb_status lattice_setup(Lattice& L, const lb_params* p, char* region);
+
+// Host-only plan of one launch's work items (the lb_plan_partition entry).
+lb_status plan_partition(const lb_params* ps, int nlat, int seg, int sms, int32_t* items,
+                         int32_t* nitems, int32_t* cta, int32_t* grid, int32_t* seg_used);
 
 // Segment length (tiles per work item) minimising the most loaded CTA.
 int choose_seg(const int* nstrips, const int* ntiles_y, int nlat, int G);

@@ -101,7 +101,7 @@ struct LatVals {
 template <typename C>
 struct alignas(128) LatDesc {
     CUtensorMap tin[2];    // 8-row block loads of buffer b: box {2 BX, 8, 9}
-    CUtensorMap tout[2];   // full-tile stores into buffer b: box {2 TX, TY, 9}
+    CUtensorMap tout[2];   // tile stores into buffer b: box {2 TX, TY, 9}, clipped at x = nx, y = ny
     Geom g;
     LatVals<C> v;
     void* fbuf[2];

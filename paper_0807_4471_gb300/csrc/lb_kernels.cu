@@ -242,9 +242,7 @@ __device__ __forceinline__ void collide(const C2 h[9], C2 out[9], C2 drho, C2 rh
 // Where a site update sends its result.
 template <typename T2>
 struct SiteOut {
-    T2* stage;             // staging tile slot of the site (full tiles), or null
-    T2* fout;              // output buffer (ragged tiles and ghost copies)
-    bool edge;             // the tile may hold sites with periodic ghost copies
+    T2* stage;             // staging tile slot of the site (step kernel)
     uint32_t key;          // stochastic rounding: hash of the lattice's step
     int obs;               // ObsKind (observe kernel) or OBS_NONE
     double* obs_out;
@@ -379,33 +377,12 @@ __device__ __forceinline__ void site_update(
         for (int i = 0; i < 9; ++i) e[i] = enc2<T2, C>(hs[i].x, hs[i].y);
     }
 
-    // Full tiles go through the staging tile and a bulk tensor store; ragged
-    // tiles and periodic ghost copies use plain stores.
+    // Every tile goes through the staging tile and leaves it by a bulk tensor
+    // store (clipped at the lattice edge); the periodic ghost copies follow
+    // by the plain stores of write_edges after the tile's barrier.
     constexpr int TX = Prec<P>::TX, TY = Prec<P>::TY;
-    if (o.stage != nullptr) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) o.stage[i * TY * TX] = e[i];
-        // staging writes before the bulk store, ahead of any global store
-        fence_proxy_async();
-    }
-    const int dX = !o.edge ? 0 : (x < 3) ? g.nx : ((x >= g.nx - 3) ? -g.nx : 0);
-    long long dY = 0;
-    if (per && o.edge)
-        dY = (y < 3) ? (long long)g.ny * g.pitch : ((y >= g.ny - 3) ? -(long long)g.ny * g.pitch : 0);
-    if (o.stage == nullptr || dX != 0 || dY != 0) {
-        const long long PL = (long long)g.rows * g.pitch;
-        T2* __restrict__ out = o.fout + (long long)(y + kGY) * g.pitch + (x + g.gx);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            T2* d = out + i * PL;
-            if (o.stage == nullptr) d[0] = e[i];
-            if (dX) d[dX] = e[i];
-            if (dY) {
-                d[dY] = e[i];
-                if (dX) d[dY + dX] = e[i];
-            }
-        }
-    }
+    for (int i = 0; i < 9; ++i) o.stage[i * TY * TX] = e[i];
     if (!per && (y == 0 || y == g.ny - 1)) {
         // x-momentum handed to the wall by the links that will bounce back
         // at the next streaming: c_x (f*_i + f_opp), f_opp = f*_i - 6 w_i
@@ -428,6 +405,58 @@ __device__ __forceinline__ void site_update(
                     if (down) red[0] += dp; else red[1] += dp;
                 }
             }
+        }
+    }
+}
+
+// Periodic images of one tile's edge sites, from the staging tile into the
+// ghost columns (x within 3 of either edge) and, when the lattice is
+// periodic in y, the ghost rows (y within 3 of either edge) and corners; by
+// all NT threads of the CTA, one (site, plane) copy each in turn, with
+// consecutive threads on consecutive sites of a plane.  The first copies go
+// to warps 2 and up: warps 0 and 1 have just issued the tile's loads and
+// store, and every warp waits for the last one at the next barrier.  Kept
+// out of the site update, whose register allocation it would otherwise
+// burden.
+template <int P, int NT>
+__device__ __forceinline__ void write_edges(const typename Prec<P>::T2* stage,
+                                            typename Prec<P>::T2* fout, const Geom& g, int x0,
+                                            int y0, bool per, int tid) {
+    typedef typename Prec<P>::T2 T2;
+    constexpr int TX = Prec<P>::TX, TY = Prec<P>::TY;
+    const int w = min(TX, g.nx - x0), h = min(TY, g.ny - y0);   // valid part of the tile
+    // source columns [0, nca) and [cb0, w), rows [0, na) and [rb0, h); the
+    // two ranges of each never meet since nx, ny >= 8
+    const int nca = max(0, min(3 - x0, w)), cb0 = max(g.nx - 3 - x0, 0), ncb = max(w - cb0, 0);
+    const int na = per ? max(0, min(3 - y0, h)) : 0;
+    const int rb0 = max(g.ny - 3 - y0, 0), nb = per ? max(h - rb0, 0) : 0;
+    const int nrow = na + nb;                 // ghost-source rows: every column
+    const int mid0 = na, mid1 = nb > 0 ? rb0 : h;   // other rows: the edge columns only
+    const int ncol = nca + ncb;
+    const int nA = nrow * w, nB = max(mid1 - mid0, 0) * ncol, n = nA + nB;
+    if (n == 0) return;
+    const long long PL = (long long)g.rows * g.pitch;
+    const long long SY = (long long)g.ny * g.pitch;
+    for (int u = tid >= 64 ? tid - 64 : tid + NT - 64; u < 9 * n; u += NT) {
+        const int i = u / n, k = u - i * n;
+        int lx, ly;
+        if (k < nA) {
+            const int r = k / w;
+            lx = k - r * w;
+            ly = r < na ? r : rb0 + (r - na);
+        } else {
+            const int kb = k - nA, r = kb / ncol, c = kb - r * ncol;
+            ly = mid0 + r;
+            lx = c < nca ? c : cb0 + (c - nca);
+        }
+        const int dX = lx < nca ? g.nx : (ncb > 0 && lx >= cb0 ? -g.nx : 0);
+        const long long dY = ly < na ? SY : (nb > 0 && ly >= rb0 ? -SY : 0);
+        const T2 e = stage[(i * TY + ly) * TX + lx];
+        T2* d = fout + i * PL + (long long)(y0 + ly + kGY) * g.pitch + (x0 + lx + g.gx);
+        if (dX) d[dX] = e;
+        if (dY) {
+            d[dY] = e;
+            if (dX) d[dY + dX] = e;
         }
     }
 }
@@ -640,9 +669,8 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
             // Phase 3: one site per thread (lx < TX): site (x0 + t_lx, y0 + t_j),
             // whose rows y - 2 .. y + 2 are window rows t_j .. t_j + 4 and whose
             // populations sit in padded rows 8 ty + 2 + t_j .. 8 ty + 4 + t_j.
-            const bool full = x0 + L::TX <= g.nx && y0 + L::TY <= g.ny;
             // only tiles within 3 sites of an edge write periodic ghost copies
-            const bool edge = !full || x0 < 3 || x0 + L::TX > g.nx - 3 ||
+            const bool edge = x0 < 3 || x0 + L::TX > g.nx - 3 ||
                               (per && (y0 < 3 || y0 + L::TY > g.ny - 3));
             {
                 const int lx = t_lx, ly = t_j;
@@ -657,9 +685,7 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
                         rr[k2] = win_r + (ly + k2) * L::RX + lx + 2;
                     }
                     SiteOut<T2> o;
-                    o.stage = full ? stage + ly * L::TX + lx : nullptr;
-                    o.fout = fout;
-                    o.edge = edge;
+                    o.stage = stage + ly * L::TX + lx;
                     o.key = key;
                     o.obs = OBS_NONE;
                     double wr[4] = {0.0, 0.0, 0.0, 0.0};
@@ -669,13 +695,15 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
                         wall[0] += wr[0];
                         wall[1] += wr[1];
                     }
+                    fence_proxy_async();   // staging writes before the bulk store
                 }
             }
             __syncthreads();
             // The bulk store and the next loads are issued by two threads of
             // different warps, side by side.
-            if (tid == kStoreThread && full) {
-                // site (x0, y0) in padded coordinates: pair column x0 + gx, row y0 + kGY
+            if (tid == kStoreThread) {
+                // site (x0, y0) in padded coordinates: pair column x0 + gx, row
+                // y0 + kGY; a ragged tile's store is clipped at x = nx, y = ny
                 tma_store_3d(&d->tout[cur ^ 1], stage, 2 * (x0 + L::GX), y0 + kGY, 0);
                 bulk_commit();
             }
@@ -685,6 +713,7 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
                 fence_proxy_async();   // generic reads of freed slots before async writes
                 while (p_pos < released + L::NB && issue_next()) {}
             }
+            if (edge) write_edges<P, L::NT>(stage, fout, g, x0, y0, per, tid);
         }
         if (bad) {   // a density of this lattice went non-finite
             atomicOr(&d->st->err, ERR_NONFINITE);
@@ -850,8 +879,6 @@ __global__ void __launch_bounds__(Layout<P>::NT)
             }
             SiteOut<T2> o;
             o.stage = nullptr;
-            o.fout = nullptr;
-            o.edge = false;
             o.key = 0u;
             o.obs = a.obs;
             o.obs_out = a.obs_out;
