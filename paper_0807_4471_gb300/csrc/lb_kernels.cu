@@ -483,21 +483,22 @@ __device__ __forceinline__ void block_sum4(double red[4], double (*s_red)[4]) {
 }
 
 // ------------------------------------------------------------ step kernel
-// Persistent and multi-lattice.  The work items of a launch are segments of
-// TX-wide column strips, `seg` tiles (TY rows each) long, over all lattices
-// (segment-major within a lattice, so that the CTAs in flight cover a band
-// of rows and halo columns are shared through L2).  CTA b takes items
-// b, b + gridDim.x, ...  Walking down a strip, a CTA keeps the 8-row blocks
-// of f* (TMA-loaded into a ring of NB slots, one block ahead of use and
-// across item boundaries) and a window of the density/Psi deviation rows
+// Persistent and multi-lattice.  The work items of a launch are runs of
+// tiles (TY rows each) down TX-wide column strips, over all lattices; CTA b
+// takes the items a.items[a.cta_items[b] .. a.cta_items[b + 1]) of a table
+// the host builds (segments dealt by estimated work in band order, or one
+// contiguous run per CTA).  Walking down a strip, a CTA keeps the 8-row
+// blocks of f* (TMA-loaded into a ring of NB slots, ahead of use and across
+// item boundaries) and a window of the density/Psi deviation rows
 // y0 - 2 .. y0 + 9 of the current tile, whose last four rows are carried
 // forward as the next tile's first four; so each block is loaded and each
 // deviation row computed once per strip, and only the x halo (4 of 64
 // columns) is redundant.  Every thread keeps one column and row of the
 // window in both phases, so all its shared-memory addresses are fixed.
-// Full tiles are written back by TMA bulk tensor stores.  The last CTA to finish advances
-// every lattice's step counter and buffer parity and takes the Couette wall
-// samples.
+// Tiles leave through a staging tile by TMA bulk tensor stores, clipped at
+// the lattice edge; tiles near an edge then write the periodic ghost copies.
+// The last CTA to finish advances every lattice's step counter and buffer
+// parity and takes the Couette wall samples.
 // V: bit 0 = every lattice periodic (no wall code); bit 1 = general forcing.
 template <int P, int V>
 __global__ void __launch_bounds__(Layout<P>::NT, 1)
