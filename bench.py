@@ -15,6 +15,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -36,10 +37,15 @@ KERNEL_SRCS = [os.path.join(ROOT, "paper_0807_4471_gb300", "csrc", f)
 
 
 def kernel_hash() -> str:
+    """sha256 (16 hex digits) of the step kernel's sources with comments and
+    runs of blank space removed: it changes with the code, not the prose."""
     h = hashlib.sha256()
     for path in KERNEL_SRCS:
-        with open(path, "rb") as fh:
-            h.update(fh.read())
+        with open(path) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 
