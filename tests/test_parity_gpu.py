@@ -7,7 +7,7 @@ max |rho|), on the plain-method configuration (Psi prefactor rho0).  The
 paper's sqrt(rho0) prefactor drives a faster demixing instability: there a
 half-ulp FP64 perturbation per step already grows to 6e-12 in 100 steps, so
 that form is held to the same tolerances at 50 steps.  Lattices span several
-tiles and ragged tails (the FP64 tile is 32 x 8 sites, the FP32/half tile 64 x 8).
+tiles and ragged tails (the FP64 tile is 28 x 8 sites, the FP32/half tile 60 x 8).
 """
 import numpy as np
 import pytest
@@ -181,6 +181,17 @@ def test_fp32_full_size_sweep_lattice(lb, O):
     st1 = g.stress()
     assert abs(st1["mass_A"] - st0["mass_A"]) / st0["mass_A"] < 1e-5
     assert abs(st1["mass_B"] - st0["mass_B"]) / st0["mass_B"] < 1e-5
+    g.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 1e-6)])
+def test_full_size_peak_lattice(lb, O, prec, tol):
+    """The largest lattice the bench times, one periodic 4096^2 lattice (69
+    strips, the last one 16 sites wide; dealt segments): two steps against
+    the oracle element by element."""
+    m = model(4096, 4096)
+    P, f, _, g = run_both(lb, O, m, 2, precision=prec, seed=3)
+    assert rel_err(gpu_pops_as_oracle(g.populations()), f) < tol
     g.close()
 
 
