@@ -66,6 +66,15 @@ int device_sms(int device) {
     return sms;
 }
 
+// L2 bytes of the current device (0 if unknown).
+static long long device_l2_bytes() {
+    int dev = 0, l2 = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
+        return 0;
+    return l2;
+}
+
 static Geom make_geom(const lb_params* p) {
     Geom g;
     const int prec = p->precision;
@@ -533,6 +542,11 @@ lb_status launch_build(Launch& Ln, Lattice* const* lats, int nlat, void* descs, 
     Ln.grid = dim3((unsigned)grid, 1, 1);
     Ln.nitems = nitems;
     Ln.seg = seg;
+    // One buffer of every lattice within 80 % of L2: the step's output can
+    // stay in L2 for the next step, next to the input streaming through.
+    long long buf = 0;
+    for (int l = 0; l < nlat; ++l) buf += (long long)lats[l]->fbytes;
+    const int l2_resident = buf * 5 <= device_l2_bytes() * 4 ? 1 : 0;
     if (prec == LB_FP64) {
         BatchArgs<double>& a = Ln.ad;
         a.k = lats[0]->kd;
@@ -544,6 +558,7 @@ lb_status launch_build(Launch& Ln, Lattice* const* lats, int nlat, void* descs, 
         a.wall_items = d_wall;
         a.slots = slots;
         a.ticket = ticket;
+        a.l2_resident = l2_resident;
     } else {
         BatchArgs<float>& a = Ln.af;
         a.k = lats[0]->kf;
@@ -555,6 +570,7 @@ lb_status launch_build(Launch& Ln, Lattice* const* lats, int nlat, void* descs, 
         a.wall_items = d_wall;
         a.slots = slots;
         a.ticket = ticket;
+        a.l2_resident = l2_resident;
     }
     return LB_OK;
 }

@@ -129,6 +129,7 @@ struct BatchArgs {
     const int* wall_items;
     double* slots;              // [nitems][2] wall-momentum partial sums
     unsigned int* ticket;       // CTA arrival counter of the launch (zero between launches)
+    int l2_resident;            // one buffer of all lattices fits in L2: cache-policy hints
 };
 
 // Observe-mode outputs (the kernel writes FP64 planes of nx*ny values).

@@ -61,14 +61,39 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
         : "memory");
 }
-// Bulk tensor store of a shared-memory box to global memory (bulk group).
-__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int x, int y,
-                                             int z) {
+// The same box load, and the bulk tensor store of a shared-memory box to
+// global memory (bulk group), with an L2 cache policy (createpolicy).
+__device__ __forceinline__ void tma_load_3d_hint(void* dst, const CUtensorMap* map, int x, int y,
+                                                 int z, uint64_t* bar, uint64_t policy) {
     asm volatile(
-        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
-            reinterpret_cast<uint64_t>(map)),
-        "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)),
+        "l"(policy)
         : "memory");
+}
+__device__ __forceinline__ void tma_store_3d_hint(const CUtensorMap* map, const void* src, int x,
+                                                  int y, int z, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group.L2::cache_hint"
+        " [%0, {%2, %3, %4}], [%1], %5;" ::"l"(reinterpret_cast<uint64_t>(map)),
+        "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_normal() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // Wait until the committed bulk stores have finished reading shared memory.
@@ -521,12 +546,19 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
     __shared__ int s_fail, s_last;
     __shared__ double s_red[L::NT / 32][4];
     __shared__ int s_wany[L::NT / 32];
+    __shared__ uint64_t s_pol[2];   // L2 policies of the block loads and the tile stores
 
     const int tid = threadIdx.x;
     const int G = gridDim.x;
     // thread 0 issues the block loads; this thread (warp 1) the bulk stores
     // of the staging tile and the waits on them
     constexpr int kStoreThread = 32;
+    // When one buffer of every lattice of the launch fits in L2 together, the
+    // step's output stays there for the next step (evict last) and the input,
+    // dead once read, goes first; otherwise both keep the normal priority.
+    // The two policies are made once, by thread 0, and kept in shared memory
+    // (held in registers through the tile loop, or made at each issue, they
+    // cost the large lattices 1-3 %).
     // window column and tile row of this thread (both phases)
     const int t_lx = tid % L::RX, t_j = tid / L::RX;
     static_assert(L::NT == L::RX * L::TY && L::TY >= 4, "one window cell per thread and row");
@@ -537,6 +569,8 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
         s_fail = 0;
         for (int b = 0; b < L::NB; ++b) mbar_init(&bars[b], 1);
         fence_mbar_init();
+        s_pol[0] = a.l2_resident ? policy_evict_first() : policy_evict_normal();
+        s_pol[1] = a.l2_resident ? policy_evict_last() : policy_evict_normal();
     }
     __syncthreads();
     // Up to here only shared memory and the host-built item tables were
@@ -567,7 +601,7 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
         uint64_t* bar = &bars[p_pos % L::NB];
         mbar_expect_tx(bar, (uint32_t)L::SLOT_BYTES);
         // box origin: pair column x0 (= x0 - gx + gx) -> element 2 x0; padded row 8j
-        tma_load_3d(slot(p_pos), p_map, 2 * p_x0, L::TYB * (p_ty_a + p_j), 0, bar);
+        tma_load_3d_hint(slot(p_pos), p_map, 2 * p_x0, L::TYB * (p_ty_a + p_j), 0, bar, s_pol[0]);
         ++p_pos;
         if (++p_j == p_nblk) {
             p_j = 0;
@@ -705,7 +739,7 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
             if (tid == kStoreThread) {
                 // site (x0, y0) in padded coordinates: pair column x0 + gx, row
                 // y0 + kGY; a ragged tile's store is clipped at x = nx, y = ny
-                tma_store_3d(&d->tout[cur ^ 1], stage, 2 * (x0 + L::GX), y0 + kGY, 0);
+                tma_store_3d_hint(&d->tout[cur ^ 1], stage, 2 * (x0 + L::GX), y0 + kGY, 0, s_pol[1]);
                 bulk_commit();
             }
             if (tid == 0) {
