@@ -444,8 +444,12 @@ def main():
                                    "one persistent launch (lattice pool, CUDA-graph replay)",
                        "nx": nx, "ny": ny, "lattices": len(rho0s),
                        "rho0": list(cfg["rho0s"]), "couplings": "Fig. 2 caption",
-                       "l2": "inputs larger than L2: the lattices' two population buffers "
-                             "(189 MB for 5 x 512^2 at FP32) are cycled every step",
+                       "l2": "inputs larger than L2, no flush: the lattices' two population "
+                             "buffers (194 MB for 5 x 512^2 at FP32) alternate every step, each "
+                             "step reading the previous step's output; when one buffer of all "
+                             "lattices fits in L2 (97 MB here) the kernel stores it evict-last, "
+                             "so part of it is still in L2 when the next step reads it, as in "
+                             "any run of consecutive steps",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk.summary(), "extra": extra,
