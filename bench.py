@@ -177,31 +177,65 @@ def cpu_oracle_sample(nx: int, ny: int, rho0: float, steps: int, seed: int):
     return nx * ny * steps / dt / 1e6, dt
 
 
+def _oracle_worker(args):
+    """One process of the parallel oracle baseline: `warm` untimed steps, then
+    `steps` timed steps of one sweep lattice (spawned: no CUDA state)."""
+    nx, ny, rho0, warm, steps, seed = args
+    import oracle as O
+    c = lbinputs.CAPTION
+    P = O.make_params(nx, ny, Ga=c["Ga"], Gr=c["Gr"], GX=c["GX"], rho0=rho0, psi_form=1)
+    f = O.init_seeded(P, seed)
+    O.run(P, f, warm)
+    t0 = time.perf_counter()
+    O.run(P, f, steps, t0=warm)
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_parallel(nx: int, ny: int, rho0s, warm: int, steps: int, seed: int):
+    """The oracle, as it stands, on several host cores at once: one process
+    per lattice (rho0s), each stepping its own lattice.  Returns (aggregate
+    MLUPS = all updates / the slowest process's time, that time, processes)."""
+    import multiprocessing as mp
+    import oracle as O
+    O.build()
+    ctx = mp.get_context("spawn")
+    jobs = [(nx, ny, r0, warm, steps, seed) for r0 in rho0s]
+    with ctx.Pool(len(jobs)) as pool:
+        dts = pool.map(_oracle_worker, jobs)
+    dt = max(dts)
+    return nx * ny * steps * len(jobs) / dt / 1e6, dt, len(jobs)
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the same workload as the GPU arm
+    -- one bench step is one LB step of every lattice of the rho0 sweep --
+    with one process per lattice on the host cores."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     cfg = lbinputs.CFG_SWEEP
     nx, ny = args.nx, args.ny
-    rho0s = cfg["rho0s"]
-    import oracle as O
-    O.build()
-    for k in range(args.warmup):
-        cpu_oracle_sample(nx, ny, rho0s[k % len(rho0s)], 1, cfg["seed"])
-    tot = 0.0
-    for k in range(args.steps):
-        _, dt = cpu_oracle_sample(nx, ny, rho0s[k % len(rho0s)], 1, cfg["seed"])
-        tot += dt
-    value = nx * ny * args.steps / tot / 1e6
-    sample = (f"one {nx}x{ny} lattice of the five-lattice rho0 sweep per step "
-              f"(rho0 cycling over {list(rho0s)}), one LB step each, FP64 oracle, 1 thread")
+    rho0s = list(cfg["rho0s"][:args.lattices])
+    value, dt, nproc = cpu_oracle_parallel(nx, ny, rho0s, args.warmup, args.steps, cfg["seed"])
+    sample = (f"all {len(rho0s)} lattices of the rho0 sweep ({nx}x{ny}, rho0 {rho0s}), "
+              f"{args.steps} timed steps after {args.warmup} warm-up steps, FP64 oracle, one "
+              f"process per lattice on {nproc} of the {host_cores()} host cores")
     line = {
         "impl": "reference", "metric": "MLUPS", "value": value, "unit": "MLUPS",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"rho0 sweep, 5 x {nx}x{ny} periodic", "nx": nx, "ny": ny},
-        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+        "config": {"workload": f"rho0 sweep, {len(rho0s)} x {nx}x{ny} periodic lattices; a bench "
+                               "step is one LB step of all of them", "nx": nx, "ny": ny,
+                   "lattices": len(rho0s), "rho0": rho0s},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": nproc, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -225,8 +259,10 @@ def peak_lattice(torch, lb, precision: str, n: int, steps: int):
 def batched_mix(torch, lb, steps: int, precision: str = "fp16"):
     """The batched workload: 64 lattices (sizes from {128, 256, 512, 1024}^2,
     rho0 in [0.55, 0.83], half Couette), FP16 offsets (or `precision`), one
-    pool launch per step.  Aggregate MLUPS over `steps` steps after a tuning
-    warm-up."""
+    pool launch per step, every lattice run for `steps` steps.  Aggregate
+    MLUPS over the whole run, CUDA events on the pool's stream around it:
+    the partition tuning on the first steps (real steps of the jobs) and the
+    CUDA-graph capture are inside."""
     jobs = lbinputs.sample_batch()
     stream = torch.cuda.Stream()
     shared = lb.make_params(128, 128, precision, psi_form=lb.LB_PSI_RHO0)
@@ -238,21 +274,22 @@ def batched_mix(torch, lb, steps: int, precision: str = "fp16"):
                                      init_shear=j["boundary"]))
     budget = sum(lb.Pool.footprint(p) for p in params) + (64 << 20)
     with lb.Pool(shared, budget, max_jobs=len(params), stream=stream) as pool:
-        ids = [pool.admit(p, j["seed"], 10 ** 6) for p, j in zip(params, jobs)]
-        pool.run(600)                    # partition tuning (about 60 steps) + warm-up
+        ids = [pool.admit(p, j["seed"], steps) for p, j in zip(params, jobs)]
         stream.synchronize()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        pool.run(steps)
+        while pool.run(steps):
+            pass
         ev1.record(stream)
         ev1.synchronize()
         dt = ev0.elapsed_time(ev1) / 1e3
         for i in ids:
-            pool.stress(i)
+            pool.stress(i)   # raises on a latched device error
         sites = sum(p.nx * p.ny for p in params)
         return {"MLUPS": sites * steps / dt / 1e6, "lattices": len(params), "sites": sites,
-                "steps": steps, "segment": pool.segment, "ms_per_step": dt / steps * 1e3,
+                "steps": steps, "seconds": dt, "segment": pool.segment,
+                "ms_per_step": dt / steps * 1e3,
                 "GB_per_s_alg": sites * steps * BYTES_PER_SITE[precision] / dt / 1e9}
 
 
@@ -302,6 +339,15 @@ def main():
     ap.add_argument("--no-peak", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--tune-steps", type=int, default=600,
+                    help="untimed set-up steps on which the pool tunes its work partition")
+    ap.add_argument("--settle-s", type=float, default=0.5,
+                    help="untimed seconds of steps before the warm-up (clock record under load)")
+    ap.add_argument("--batch-steps", type=int, default=lbinputs.CFG_BATCH_STEPS,
+                    help="steps of every lattice of the 64-lattice batch")
+    ap.add_argument("--serve-jobs", type=int, default=2000)
+    ap.add_argument("--serve-scale", type=float, default=0.1,
+                    help="factor on the served jobs' step counts")
     ap.add_argument("--lattices", type=int, default=len(lbinputs.CFG_SWEEP["rho0s"]),
                     help="number of sweep lattices stepped per bench step (profiling runs)")
     args = ap.parse_args()
@@ -333,21 +379,35 @@ def main():
     budget = sum(lb.Pool.footprint(lb.make_params(nx, ny, prec, rho0=r0, psi_form=lb.LB_PSI_RHO0))
                  for r0 in rho0s) + (64 << 20)
     pool = lb.Pool(shared, budget, max_jobs=len(rho0s), stream=stream)
-    total_steps = args.warmup + args.steps + 1
+    # members run until released: the untimed set-up, warm-up, timed and
+    # end-to-end steps all come out of one long schedule
     jobs = [pool.admit(lb.make_params(nx, ny, prec, rho0=r0, psi_form=lb.LB_PSI_RHO0),
-                       cfg["seed"], total_steps) for r0 in rho0s]
-    pool.run(args.warmup)          # includes the partition tuning on the first steps
-    stream.synchronize()
+                       cfg["seed"], 1 << 40) for r0 in rho0s]
 
     def barrier():
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    # The clock record spans the set-up, the warm-up and the timed steps, so
+    # that a short timed region still has samples taken under load.
     with ClockSampler(local) as clk:
+        # Set-up, untimed: the pool's autotuner times its candidate
+        # partitions on the first steps of the member set (real steps), then
+        # the launch of the chosen partition is captured into a CUDA graph.
+        pool.run(args.tune_steps)
+        pool.prepare()
+        stream.synchronize()
+        # untimed steps until the sampler has seen the GPU under load
+        settle, t_set = 0, time.perf_counter()
+        while time.perf_counter() - t_set < args.settle_s:
+            pool.run(1024)
+            stream.synchronize()
+            settle += 1024
+        pool.run(args.warmup)
+        barrier()
         ev0.record(stream)
         pool.run(args.steps)
         ev1.record(stream)
@@ -370,11 +430,12 @@ def main():
                 "bytes_per_launch_alg": BYTES_PER_SITE[prec] * sites,
                 "kernel": f"k_step<{prec}> (all {len(rho0s)} lattices per launch)",
                 "avg_launch_us": avg_launch * 1e6, "segment": pool.segment}
+    pool_segment = pool.segment
 
     # End to end through the public API with host buffers: restart the same
     # pool members from FP64 fields in pinned host memory (host -> device),
-    # take the steps, read rho_A and rho_B back (device -> host); the pool's
-    # partition was tuned on the warm-up steps above.
+    # take the steps, read rho_A and rho_B back (device -> host); the member
+    # set, its tuned partition and its graph are the ones timed above.
     e2e = None
     if not args.no_e2e:
         def pinned(shape):
@@ -414,21 +475,27 @@ def main():
             mlups, gbs = peak_lattice(torch, lb, p, lbinputs.CFG_PEAK["nx"], 50)
             extra[f"peak_{p}_4096"] = {"MLUPS": mlups, "GB_per_s_alg": gbs,
                                        "frac_hbm": gbs / hbm_peak}
-        extra["batched_64_fp16"] = batched_mix(torch, lb, 40)
-        extra["batched_64_fp32"] = batched_mix(torch, lb, 40, "fp32")
+        extra["batched_64_fp16"] = batched_mix(torch, lb, args.batch_steps)
+        extra["batched_64_fp32"] = batched_mix(torch, lb, args.batch_steps, "fp32")
         if not args.no_serve:
             # the same arrival stream (rate set by the FP16 batched capacity) for both
             cap = extra["batched_64_fp16"]["MLUPS"]
-            extra["serving"] = serving(torch, lb, 300, 0.01, 0.8, cap)
-            extra["serving_fp32"] = serving(torch, lb, 300, 0.01, 0.8, cap, "fp32")
+            extra["serving"] = serving(torch, lb, args.serve_jobs, args.serve_scale, 0.8, cap)
+            extra["serving_fp32"] = serving(torch, lb, args.serve_jobs, args.serve_scale, 0.8,
+                                            cap, "fp32")
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         steps_cpu = 60
         mlups, cdt = cpu_oracle_sample(nx, ny, 0.70, steps_cpu, cfg["seed"])
-        cpu = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-               "sample": f"one {nx}x{ny} lattice (rho0 0.70) of the sweep, {steps_cpu} steps, "
-                         f"{cdt:.1f} s, FP64 oracle single thread"}
+        par, pdt, nproc = cpu_oracle_parallel(nx, ny, rho0s, 0, 30, cfg["seed"])
+        cpu = {"value": par, "unit": "MLUPS", "cores": nproc, "kind": "oracle",
+               "sample": f"the {len(rho0s)} lattices of the sweep ({nx}x{ny}), one process per "
+                         f"lattice on {nproc} of the {host_cores()} host cores, 30 steps each, "
+                         f"{pdt:.1f} s; FP64 oracle as it stands",
+               "single_core": {"value": mlups, "unit": "MLUPS", "cores": 1,
+                               "sample": f"one {nx}x{ny} lattice (rho0 0.70), {steps_cpu} steps, "
+                                         f"{cdt:.1f} s, one thread"}}
 
     if rank == 0:
         line = {
@@ -450,7 +517,11 @@ def main():
                              "lattices fits in L2 (97 MB here) the kernel stores it evict-last, "
                              "so part of it is still in L2 when the next step reads it, as in "
                              "any run of consecutive steps",
-                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "setup": f"untimed before the warm-up: {args.tune_steps} steps of "
+                                "partition autotuning, CUDA-graph capture of the chosen launch, "
+                                f"{settle} steps while the clock sampler starts",
+                       "partition": pool_segment},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk.summary(), "extra": extra,
         }

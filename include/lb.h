@@ -242,6 +242,15 @@ lb_status lb_pool_admit(lb_pool* pool, const lb_params* p, uint64_t seed, int64_
  * Asynchronous except for re-partitioning and tuning. */
 lb_status lb_pool_run(lb_pool* pool, int64_t quantum, int32_t* active);
 
+/* Set up the step launch of the current member set without taking a step:
+ * build its work partition (the cached tuned one, the fixed one of
+ * lb_pool_set_partition, or else the load-balance model's -- no tuning) and
+ * capture its CUDA graph, so that the next lb_pool_run replays the graph
+ * with no capture or instantiation in its way.  A later lb_pool_run on the
+ * same member set keeps this partition.  Synchronises the pool stream when
+ * it builds; LB_OK with nothing to do when no member has steps left. */
+lb_status lb_pool_prepare(lb_pool* pool);
+
 /* Steps done and whether the member has finished (all its steps). */
 lb_status lb_pool_poll(lb_pool* pool, lb_job job, int64_t* steps_done, int32_t* done);
 
@@ -311,7 +320,9 @@ lb_status lb_plan_partition(const lb_params* ps, int32_t nlat, int32_t seg, int3
  * device array of 128 KB + 256 B that every GPU which loads the library keeps
  * until the process exits.  The first call on a device looks up that array's
  * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  Each call clears the counter with cudaMemsetAsync on
+ * stream capture.  The address is kept per device and context: after a
+ * cudaDeviceReset the next call on the new context looks it up again (and is
+ * then again a first call).  Each call clears the counter with cudaMemsetAsync on
  * `stream` and overwrites the slots it uses.  All calls on a device share the
  * array, so calls whose kernels may overlap on the GPU (different streams with
  * no ordering between them) race: order them on one stream or with events. */
@@ -325,6 +336,18 @@ lb_status lb_totals_noalloc(int32_t nx, int32_t ny, const double* rho_A, const d
  * stays usable.  Any other status means the wait or the error path is
  * broken.  Allocates (and frees) one word of device memory. */
 lb_status lb_selftest_wait(void* stream, int32_t limit);
+
+/* Diagnostic, no counterpart in the paper: evaluates the FP32 functions the
+ * step kernel uses for the pseudo-potential and the velocities -- its
+ * exp(x) - 1 (Cody-Waite reduction x = k ln 2 + r, degree-7 Taylor series of
+ * expm1(r), about 2 ulp) and its reciprocal (rcp.approx.ftz, within 1 ulp)
+ * -- on n caller values, next to the CUDA library's expm1f, so that their
+ * error can be measured over the arguments the kernel sees.  x: device
+ * array of n floats; out: device array of 3 n floats, receiving
+ * {pexpm1(x[k]), expm1f(x[k]), recip(x[k])} at out[3k .. 3k + 2] (reciprocal
+ * flushes subnormal results to zero).  Asynchronous on `stream`;
+ * LB_ERR_INVALID for n < 0 or a NULL pointer with n > 0. */
+lb_status lb_selftest_math(const float* x, float* out, int64_t n, void* stream);
 
 /* Static description of a status code. */
 const char* lb_status_string(lb_status s);

@@ -28,6 +28,8 @@ CFG_SWEEP = dict(nx=512, ny=512, seed=1, rho0s=(0.55, 0.65, 0.70, 0.75, 0.83),
 CFG_COUETTE = dict(nx=512, ny=512, seed=2, rho0=0.70, steps=200_000)
 # Peak-bandwidth lattice.
 CFG_PEAK = dict(nx=4096, ny=4096, seed=5)
+# Batched: steps of every lattice of the 64-lattice mix.
+CFG_BATCH_STEPS = 20_000
 
 
 def couette_shear_rates(n: int = 8, lo: float = 1e-6, hi: float = 1e-4):

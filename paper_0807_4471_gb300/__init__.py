@@ -102,6 +102,7 @@ def load():
             "lb_pool_create": (C.c_int, [P, C.c_size_t, C.c_int32, C.c_void_p, C.POINTER(H)]),
             "lb_pool_admit": (C.c_int, [H, P, C.c_uint64, C.c_int64, C.POINTER(C.c_int32)]),
             "lb_pool_run": (C.c_int, [H, C.c_int64, C.POINTER(C.c_int32)]),
+            "lb_pool_prepare": (C.c_int, [H]),
             "lb_pool_poll": (C.c_int, [H, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
             "lb_pool_fields": (C.c_int, [H, C.c_int32, dp, dp, dp, dp]),
             "lb_pool_init_fields": (C.c_int, [H, C.c_int32, dp, dp, dp, dp]),
@@ -109,6 +110,7 @@ def load():
             "lb_pool_release": (C.c_int, [H, C.c_int32]),
             "lb_pool_segment": (C.c_int32, [H]),
             "lb_selftest_wait": (C.c_int, [H, C.c_int32]),
+            "lb_selftest_math": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
             "lb_pool_set_partition": (C.c_int, [H, C.c_int32]),
             "lb_pool_destroy": (C.c_int, [H]),
             "lb_plan_partition": (C.c_int, [C.POINTER(lb_params), C.c_int32, C.c_int32, C.c_int32,
@@ -246,6 +248,10 @@ def lb_pool_run(pool: int, quantum: int) -> int:
     return n.value
 
 
+def lb_pool_prepare(pool: int):
+    _check(load().lb_pool_prepare(C.c_void_p(pool)), "lb_pool_prepare")
+
+
 def lb_pool_poll(pool: int, job: int):
     steps, done = C.c_int64(), C.c_int32()
     _check(load().lb_pool_poll(C.c_void_p(pool), job, C.byref(steps), C.byref(done)),
@@ -276,6 +282,12 @@ def lb_pool_release(pool: int, job: int):
 def lb_selftest_wait(limit: int = 1024, stream: int = 0) -> int:
     """Status of the bounded-wait self-test (LB_ERR_TIMEOUT when it works)."""
     return load().lb_selftest_wait(C.c_void_p(stream), limit)
+
+
+def lb_selftest_math(x_ptr: int, out_ptr: int, n: int, stream: int = 0):
+    """Device pointers: n FP32 arguments in, 3 n FP32 values out (see include/lb.h)."""
+    _check(load().lb_selftest_math(C.c_void_p(x_ptr), C.c_void_p(out_ptr), n, C.c_void_p(stream)),
+           "lb_selftest_math")
 
 
 def lb_pool_segment(pool: int) -> int:
@@ -445,6 +457,11 @@ class Pool:
 
     def run(self, quantum: int) -> int:
         return lb_pool_run(self.h, quantum)
+
+    def prepare(self):
+        """Build the current member set's launch and capture its graph
+        without stepping (see lb_pool_prepare)."""
+        lb_pool_prepare(self.h)
 
     def poll(self, job: int):
         return lb_pool_poll(self.h, job)

@@ -236,6 +236,12 @@ lb_status lb_selftest_wait(void* stream, int32_t limit) {
     return (h & ERR_TIMEOUT) ? LB_ERR_TIMEOUT : LB_OK;
 }
 
+lb_status lb_selftest_math(const float* x, float* out, int64_t n, void* stream) {
+    if (n < 0 || (n > 0 && (!x || !out))) return LB_ERR_INVALID;
+    if (n == 0) return LB_OK;
+    return cuda_status(launch_math_probe(x, out, (long long)n, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 const char* lb_status_string(lb_status s) {
     switch (s) {
         case LB_OK: return "ok";

@@ -31,6 +31,8 @@ enum : unsigned int { ERR_NONFINITE = 1u, ERR_TIMEOUT = 2u };
 
 // The bounded-wait self-test kernel (lb_selftest_wait).
 cudaError_t launch_wait_selftest(unsigned int* err, int limit, cudaStream_t s);
+// The FP32 exp(x) - 1 / reciprocal probe (lb_selftest_math).
+cudaError_t launch_math_probe(const float* x, float* out, long long n, cudaStream_t s);
 
 // Geometry of the ghost-padded population planes.  Plane i (i = 0..8, the
 // D2Q9 direction) holds (ny + 2*kGY) rows of `pitch` interleaved (A, B)

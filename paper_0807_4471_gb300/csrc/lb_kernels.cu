@@ -788,8 +788,13 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
     }
     if (tid == kStoreThread) bulk_wait_all();
     if (s_fail && tid == 0) {
-        // let copies in flight land before the CTA exits
-        for (int b = 0; b < L::NB; ++b) mbar_wait_bounded(&bars[b], 0), mbar_wait_bounded(&bars[b], 1);
+        // Let copies in flight land before the CTA exits.  No slot is
+        // re-armed once a wait has failed, so the last NB positions issued
+        // are each slot's latest arm, and every earlier one has landed; wait
+        // on each of those once, with its own phase parity (a position that
+        // has landed returns at once).
+        for (int pos = p_pos > L::NB ? p_pos - L::NB : 0; pos < p_pos; ++pos)
+            mbar_wait_bounded(&bars[pos % L::NB], (pos / L::NB) & 1);
     }
     if (s_fail && tid == 0)   // report on every lattice of the launch
         for (int l = 0; l < a.nlat; ++l) atomicOr(&a.lat[l].st->err, ERR_TIMEOUT);
@@ -1024,6 +1029,27 @@ __global__ void k_load_pops(Geom g, typename Prec<P>::C rho_ref, typename Prec<P
 // kernel latches ERR_TIMEOUT in *err and returns, leaving the context usable.
 // (Compiled in the FP32 translation unit only.)
 #if LB_PREC == 1
+// ------------------------------------------------------ FP32 math probe
+// The step kernel's FP32 exp(x) - 1 and reciprocal on caller values, next
+// to the CUDA library's expm1f: out[3k] = pexpm1(x[k]), out[3k + 1] =
+// expm1f(x[k]), out[3k + 2] = recip(x[k]) (x[k] taken in pairs, as the
+// kernel does; an odd tail element is paired with itself).
+__global__ void k_math_probe(const float* __restrict__ x, float* __restrict__ out, long long n) {
+    for (long long k = 2 * (blockIdx.x * (long long)blockDim.x + threadIdx.x); k < n;
+         k += 2LL * gridDim.x * blockDim.x) {
+        const float a = x[k], b = k + 1 < n ? x[k + 1] : a;
+        const float2 e = pexpm1(make_float2(a, b));
+        out[3 * k] = e.x;
+        out[3 * k + 1] = expm1f(a);
+        out[3 * k + 2] = recip(a);
+        if (k + 1 < n) {
+            out[3 * k + 3] = e.y;
+            out[3 * k + 4] = expm1f(b);
+            out[3 * k + 5] = recip(b);
+        }
+    }
+}
+
 __global__ void k_wait_selftest(unsigned int* err, int limit) {
     __shared__ __align__(8) uint64_t bar;
     if (threadIdx.x == 0) {
@@ -1167,6 +1193,12 @@ template cudaError_t launch_init_prec<LB_PREC>(const Geom&, const void*, void*, 
 namespace lbgb {
 cudaError_t launch_wait_selftest(unsigned int* err, int limit, cudaStream_t s) {
     k_wait_selftest<<<1, 32, 0, s>>>(err, limit);
+    return cudaGetLastError();
+}
+cudaError_t launch_math_probe(const float* x, float* out, long long n, cudaStream_t s) {
+    long long blocks = (n + 511) / 512;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_math_probe<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, s>>>(x, out, n);
     return cudaGetLastError();
 }
 }  // namespace lbgb

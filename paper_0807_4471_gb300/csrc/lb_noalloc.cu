@@ -101,22 +101,65 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// Device address of the scratch array, looked up once per device.
+// Unique id of the calling thread's current context (cuCtxGetId: unique over
+// the life of the process, unlike the CUcontext handle, which a context
+// created after a device reset may reuse).  False when there is no current
+// context yet or the driver does not offer the call.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+bool current_context_id(unsigned long long* id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void* a = nullptr;
+        void* b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) ==
+                cudaSuccess && qa == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) ==
+                cudaSuccess && qb == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<CtxGetCurrentFn>(a);
+            get_id = reinterpret_cast<CtxGetIdFn>(b);
+        }
+        cudaGetLastError();
+        looked_up = true;
+    }
+    CUcontext ctx = nullptr;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device address of the scratch array, looked up once per device and
+// context: a context created after a device reset loads the module again,
+// possibly elsewhere, so its address is looked up afresh.
 std::mutex g_mu;
 void* g_addr[64] = {nullptr};
+unsigned long long g_ctx[64] = {0};
 
 lb_status scratch_address(NoAllocScratch** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LB_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    unsigned long long id = 0;
+    bool have_id = current_context_id(&id);
+    if (!g_addr[dev] || !have_id || g_ctx[dev] != id) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
             return LB_ERR_CUDA;
         }
+        // the lookup made the device's primary context current if it was not
+        if (!have_id) have_id = current_context_id(&id);
         g_addr[dev] = p;
+        g_ctx[dev] = have_id ? id : 0;
+        if (!have_id) {   // no context id to key on: look up again next call
+            *out = reinterpret_cast<NoAllocScratch*>(p);
+            g_addr[dev] = nullptr;
+            return LB_OK;
+        }
     }
     *out = reinterpret_cast<NoAllocScratch*>(g_addr[dev]);
     return LB_OK;

@@ -168,27 +168,34 @@ lb_status build(lb_pool* P, int seg) {
     return s;
 }
 
+// Capture kGraphChunk launches of the built launch into the pool's graph
+// (nothing executes during the capture).
+lb_status capture_graph(lb_pool* P) {
+    if (P->graph) return LB_OK;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_status(e);
+    lb_status s = LB_OK;
+    for (int i = 0; i < kGraphChunk && s == LB_OK; ++i) s = launch_run(P->launch, P->stream);
+    e = cudaStreamEndCapture(P->stream, &g);
+    if (s != LB_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&P->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        P->graph = nullptr;
+        return cuda_status(e);
+    }
+    return LB_OK;
+}
+
 // Run k steps of the built launch: captured chunks, then single launches.
 lb_status run_steps(lb_pool* P, long long k) {
     while (k >= kGraphChunk) {
-        if (!P->graph) {
-            cudaGraph_t g = nullptr;
-            cudaError_t e = cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal);
-            if (e != cudaSuccess) return cuda_status(e);
-            lb_status s = LB_OK;
-            for (int i = 0; i < kGraphChunk && s == LB_OK; ++i) s = launch_run(P->launch, P->stream);
-            e = cudaStreamEndCapture(P->stream, &g);
-            if (s != LB_OK) {
-                if (g) cudaGraphDestroy(g);
-                return s;
-            }
-            if (e == cudaSuccess) e = cudaGraphInstantiate(&P->graph, g, 0);
-            if (g) cudaGraphDestroy(g);
-            if (e != cudaSuccess) {
-                P->graph = nullptr;
-                return cuda_status(e);
-            }
-        }
+        lb_status s = capture_graph(P);
+        if (s != LB_OK) return s;
         cudaError_t e = cudaGraphLaunch(P->graph, P->stream);
         if (e != cudaSuccess) return cuda_status(e);
         k -= kGraphChunk;
@@ -259,9 +266,39 @@ long long tune(lb_pool* P, long long budget_steps, lb_status* st) {
     return used;
 }
 
+// Members with steps left (in slot order), and the largest step count, up to
+// `limit`, that all of them can take.
+long long active_members(lb_pool* P, long long limit, std::vector<int>& act) {
+    act.clear();
+    long long k = limit;
+    for (size_t j = 0; j < P->members.size(); ++j) {
+        const Member& m = P->members[j];
+        if (m.used && m.done < m.target) {
+            act.push_back((int)j);
+            k = std::min(k, m.target - m.done);
+        }
+    }
+    return k;
+}
+
 }  // namespace
 
 extern "C" {
+
+lb_status lb_pool_prepare(lb_pool* P) {
+    if (!P) return LB_ERR_INVALID;
+    std::vector<int> act;
+    active_members(P, 1, act);
+    if (act.empty()) return LB_OK;
+    if (!P->built || act != P->active) {
+        P->active = act;
+        auto it = P->tuned.find(signature(P));
+        const int seg = P->forced_seg != 0 ? P->forced_seg : (it != P->tuned.end() ? it->second : 0);
+        lb_status s = build(P, seg);
+        if (s != LB_OK) return s;
+    }
+    return capture_graph(P);
+}
 
 lb_status lb_pool_footprint(const lb_params* p, size_t* bytes) {
     lb_status s = validate_params(p);
@@ -360,14 +397,7 @@ lb_status lb_pool_run(lb_pool* P, int64_t quantum, int32_t* active_out) {
     lb_status s = LB_OK;
     while (remaining > 0) {
         std::vector<int> act;
-        long long k = remaining;
-        for (size_t j = 0; j < P->members.size(); ++j) {
-            const Member& m = P->members[j];
-            if (m.used && m.done < m.target) {
-                act.push_back((int)j);
-                k = std::min(k, m.target - m.done);
-            }
-        }
+        long long k = active_members(P, remaining, act);
         if (act.empty()) break;
         if (!P->built || act != P->active) {
             P->active = act;

@@ -47,6 +47,8 @@ class Job:
 
 @dataclass
 class Stats:
+    """Job counts: every admitted job ends once, as finished (a result),
+    failed (an error) or cancelled; site_updates counts finished jobs only."""
     admitted: int = 0
     finished: int = 0
     failed: int = 0
@@ -172,13 +174,15 @@ class Server:
                 job.result = res
             except LbError as e:
                 job.error = str(e)
-                self.stats.failed += 1
             self.pool.release(slot)
             job.finished = self.clock()
             del self.running[slot]
             self.done.append(job)
-            self.stats.finished += 1
-            self.stats.site_updates += int(job.spec["nx"]) * int(job.spec["ny"]) * steps
+            if job.error is None:
+                self.stats.finished += 1
+                self.stats.site_updates += int(job.spec["nx"]) * int(job.spec["ny"]) * steps
+            else:   # its steps produced no result: neither finished nor counted
+                self.stats.failed += 1
             self._log(job)
 
     def step(self) -> int:

@@ -130,3 +130,26 @@ def test_cancel_queued_and_running_jobs_and_log(lb, tmp_path):
     assert sorted(r["id"] for r in recs) == sorted([a.id, b.id, c.id, d.id])
     assert {r["id"]: r["error"] for r in recs}[a.id] == "cancelled"
     assert all(r["latency"] is not None for r in recs)
+
+
+def test_failed_result_is_not_counted_as_finished(lb):
+    """A job whose result cannot be read (a latched device error) counts as
+    failed only: not as finished, and its steps add no site updates."""
+    from paper_0807_4471_gb300.serve import Server
+
+    class BadStressPool(FakePool):
+        def stress(self, j):
+            if self.jobs[j]["need"] == 16 * 16:
+                raise self.lb.LbError(self.lb.LB_ERR_NONFINITE, "stress")
+            return super().stress(j)
+
+    pool = BadStressPool(10 ** 6, lb)
+    srv = Server(pool, make, quantum=10)
+    good = srv.submit(dict(nx=8, ny=8, steps=20), arrival=0.0)
+    bad = srv.submit(dict(nx=16, ny=16, steps=20), arrival=0.0)
+    srv.run_until_idle()
+    assert good.result is not None and good.error is None
+    assert bad.result is None and bad.error is not None and "status -4" in bad.error
+    assert srv.stats.finished == 1 and srv.stats.failed == 1
+    assert srv.stats.site_updates == 8 * 8 * 20
+    assert pool.used == 0
