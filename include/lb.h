@@ -107,7 +107,10 @@ typedef struct {
     double kolmo_amp;          /* Kolmogorov acceleration amplitude            */
     double kolmo_k;            /* a_x += kolmo_amp sin(2 pi kolmo_k y / ny)    */
     int32_t rounding;          /* lb_rounding of the half formats              */
-    int32_t reserved0;         /* must be 0                                    */
+    int32_t tile_rows;         /* step-kernel tile height of an lb_create handle:
+                                  0 = library default, 8 (one site per thread)
+                                  or 16 (two per thread; not LB_FP64); results
+                                  are bitwise the same; pools choose their own */
 } lb_params;
 
 typedef struct {
@@ -278,6 +281,16 @@ int32_t lb_pool_segment(const lb_pool* pool);
  * CTA, 0 back to autotuning.  Applies from the next lb_pool_run. */
 lb_status lb_pool_set_partition(lb_pool* pool, int32_t seg);
 
+/* Tile height of the step kernel: the autotuner times both tile shapes (8
+ * rows, one site per thread; 16 rows, two vertically adjacent sites per
+ * thread sharing their stencil rows -- not for FP64) together with the
+ * partitions.  lb_pool_set_tile_rows fixes it (8 or 16; 0 back to
+ * autotuning; LB_ERR_INVALID for a shape the pool's precision lacks), from
+ * the next lb_pool_run; lb_pool_tile_rows returns the current launch's, or
+ * 0 if none is built.  Every shape gives bitwise the same results. */
+lb_status lb_pool_set_tile_rows(lb_pool* pool, int32_t rows);
+int32_t lb_pool_tile_rows(const lb_pool* pool);
+
 lb_status lb_pool_destroy(lb_pool* pool);
 
 /* Host only, no device work (usable without a GPU): the work items that one
@@ -285,8 +298,8 @@ lb_status lb_pool_destroy(lb_pool* pool);
  * on a device with `sms` SMs.  seg > 0: segments of seg tiles, each given in
  * band order to the CTA with the least estimated work; -1: one cost-balanced
  * contiguous run of tiles per CTA; 0: the library's default for these sizes.
- * A tile is TX x TY sites (60 x 8; 28 x 8 for FP64), a strip a TX-wide
- * column of tiles.  On entry *nitems is the capacity of `items` (in items of
+ * A tile is TX x tile_rows sites (TX = 60; 28 for FP64), a strip a TX-wide
+ * column of tiles; tile_rows is 8 (or 0, meaning 8) or 16 (not for FP64).  On entry *nitems is the capacity of `items` (in items of
  * 4 int32: lattice index, strip, first tile row, end tile row) and *grid the
  * capacity of `cta` (in entries); on return they hold the item count and the
  * number of CTAs, items lists the items CTA by CTA, the items of CTA b are
@@ -294,9 +307,9 @@ lb_status lb_pool_destroy(lb_pool* pool);
  * partition applied.  LB_ERR_INVALID for an invalid lattice, mixed
  * precisions, nlat or sms < 1, or a capacity too small (the sizes needed
  * are still returned).  No pointer is retained. */
-lb_status lb_plan_partition(const lb_params* ps, int32_t nlat, int32_t seg, int32_t sms,
-                            int32_t* items, int32_t* nitems, int32_t* cta, int32_t* grid,
-                            int32_t* seg_used);
+lb_status lb_plan_partition(const lb_params* ps, int32_t nlat, int32_t seg, int32_t tile_rows,
+                            int32_t sms, int32_t* items, int32_t* nitems, int32_t* cta,
+                            int32_t* grid, int32_t* seg_used);
 
 /* Largest lattice, nx * ny, that lb_totals_noalloc accepts (4096 x 4096). */
 #define LB_NOALLOC_MAX_SITES 16777216

@@ -42,7 +42,7 @@ class lb_params(C.Structure):
         ("G_X", C.c_double), ("rho0", C.c_double), ("u_wall", C.c_double),
         ("init_amp", C.c_double), ("rho_ref", C.c_double), ("g_x", C.c_double),
         ("kolmo_amp", C.c_double), ("kolmo_k", C.c_double), ("rounding", C.c_int32),
-        ("reserved0", C.c_int32),
+        ("tile_rows", C.c_int32),
     ]
 
 
@@ -112,9 +112,11 @@ def load():
             "lb_selftest_wait": (C.c_int, [H, C.c_int32]),
             "lb_selftest_math": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
             "lb_pool_set_partition": (C.c_int, [H, C.c_int32]),
+            "lb_pool_set_tile_rows": (C.c_int, [H, C.c_int32]),
+            "lb_pool_tile_rows": (C.c_int32, [H]),
             "lb_pool_destroy": (C.c_int, [H]),
             "lb_plan_partition": (C.c_int, [C.POINTER(lb_params), C.c_int32, C.c_int32, C.c_int32,
-                                            C.c_void_p, C.POINTER(C.c_int32), C.c_void_p,
+                                            C.c_int32, C.c_void_p, C.POINTER(C.c_int32), C.c_void_p,
                                             C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
         }
         for name, (res, args) in sig.items():
@@ -298,11 +300,19 @@ def lb_pool_set_partition(pool: int, seg: int):
     _check(load().lb_pool_set_partition(C.c_void_p(pool), seg), "lb_pool_set_partition")
 
 
+def lb_pool_set_tile_rows(pool: int, rows: int):
+    _check(load().lb_pool_set_tile_rows(C.c_void_p(pool), rows), "lb_pool_set_tile_rows")
+
+
+def lb_pool_tile_rows(pool: int) -> int:
+    return load().lb_pool_tile_rows(C.c_void_p(pool))
+
+
 def lb_pool_destroy(pool: int):
     _check(load().lb_pool_destroy(C.c_void_p(pool)), "lb_pool_destroy")
 
 
-def lb_plan_partition(params, seg: int = 0, sms: int = 152):
+def lb_plan_partition(params, seg: int = 0, sms: int = 152, tile_rows: int = 8):
     """Host-only work plan of one step launch over the lattices `params`:
     (items int32[n, 4] = lattice, strip, first tile row, end tile row;
     cta int32[grid + 1] offsets into items; the partition applied)."""
@@ -310,16 +320,17 @@ def lb_plan_partition(params, seg: int = 0, sms: int = 152):
     L = load()
     arr = (lb_params * len(params))(*params)
     ni, ng, su = C.c_int32(0), C.c_int32(0), C.c_int32(0)
-    L.lb_plan_partition(arr, len(params), seg, sms, None, C.byref(ni), None, C.byref(ng),
-                        C.byref(su))
+    L.lb_plan_partition(arr, len(params), seg, tile_rows, sms, None, C.byref(ni), None,
+                        C.byref(ng), C.byref(su))
     if ni.value < 1 or ng.value < 1:
         raise LbError(LB_ERR_INVALID, "lb_plan_partition")
     items = np.zeros((ni.value, 4), dtype=np.int32)
     cta = np.zeros(ng.value + 1, dtype=np.int32)
     ni.value, ng.value = items.shape[0], cta.shape[0]
-    _check(L.lb_plan_partition(arr, len(params), seg, sms, items.ctypes.data_as(C.c_void_p),
-                               C.byref(ni), cta.ctypes.data_as(C.c_void_p), C.byref(ng),
-                               C.byref(su)), "lb_plan_partition")
+    _check(L.lb_plan_partition(arr, len(params), seg, tile_rows, sms,
+                               items.ctypes.data_as(C.c_void_p), C.byref(ni),
+                               cta.ctypes.data_as(C.c_void_p), C.byref(ng), C.byref(su)),
+           "lb_plan_partition")
     return items, cta, su.value
 
 
@@ -490,6 +501,14 @@ class Pool:
     def set_partition(self, seg: int):
         """Fix the work partition (seg > 0 segments, -1 contiguous runs, 0 autotune)."""
         lb_pool_set_partition(self.h, seg)
+
+    def set_tile_rows(self, rows: int):
+        """Fix the step kernel's tile height (8 or 16; 0 autotune)."""
+        lb_pool_set_tile_rows(self.h, rows)
+
+    @property
+    def tile_rows(self) -> int:
+        return lb_pool_tile_rows(self.h)
 
     def close(self):
         if getattr(self, "h", None):

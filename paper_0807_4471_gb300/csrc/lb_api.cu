@@ -63,10 +63,12 @@ lb_status create_common(const lb_params* p, void* stream, void* ws, size_t bytes
     if (s == LB_OK) {
         Lattice* one = &h->lat;
         alignas(128) unsigned char scratch[sizeof(LatDesc<double>)];
+        const int spt = p->tile_rows == 0 ? default_spt(p->precision)
+                                           : p->tile_rows / kernel_tile_y(p->precision);
         s = launch_build(h->launch, &one, 1, h->ws + H.desc,
                          reinterpret_cast<double*>(h->ws + H.slots),
                          reinterpret_cast<unsigned int*>(h->ws + H.ticket), device_sms(h->device),
-                         h->stream, scratch);
+                         h->stream, scratch, 0, spt);
     }
     if (s != LB_OK) {
         if (owns) cudaFree(ws);
@@ -256,10 +258,10 @@ const char* lb_status_string(lb_status s) {
     return "unknown status";
 }
 
-lb_status lb_plan_partition(const lb_params* ps, int32_t nlat, int32_t seg, int32_t sms,
-                            int32_t* items, int32_t* nitems, int32_t* cta, int32_t* grid,
-                            int32_t* seg_used) {
-    return lbgb::plan_partition(ps, nlat, seg, sms, items, nitems, cta, grid, seg_used);
+lb_status lb_plan_partition(const lb_params* ps, int32_t nlat, int32_t seg, int32_t tile_rows,
+                            int32_t sms, int32_t* items, int32_t* nitems, int32_t* cta,
+                            int32_t* grid, int32_t* seg_used) {
+    return lbgb::plan_partition(ps, nlat, seg, tile_rows, sms, items, nitems, cta, grid, seg_used);
 }
 
 }  // extern "C"

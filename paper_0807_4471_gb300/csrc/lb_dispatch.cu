@@ -21,8 +21,9 @@ int kernel_elem_bytes(int p) { LB_SWITCH(p, return (int)sizeof(typename Layout<P
 int kernel_smem_obs_bytes(int p) { LB_SWITCH(p, return Layout<P>::SMEM_OBS) return 0; }
 int kernel_block_rows(int p) { LB_SWITCH(p, return Layout<P>::TYB) return 0; }
 
-cudaError_t launch_step(int precision, const void* args, int variant, dim3 grid, cudaStream_t s) {
-    LB_SWITCH(precision, return launch_step_prec<P>(args, variant, grid, s))
+cudaError_t launch_step(int precision, const void* args, int variant, int spt, dim3 grid,
+                        cudaStream_t s) {
+    LB_SWITCH(precision, return launch_step_prec<P>(args, variant, spt, grid, s))
     return cudaErrorInvalidValue;
 }
 

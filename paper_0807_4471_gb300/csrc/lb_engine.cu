@@ -42,7 +42,8 @@ lb_status validate_params(const lb_params* p) {
     if (!(p->tau_A > 0.5) || !(p->tau_B > 0.5) || !(p->rho0 > 0.0)) return LB_ERR_INVALID;
     if (p->stress_every < 1 || p->stress_t0 < 0) return LB_ERR_INVALID;
     if (p->rounding != LB_ROUND_NEAREST && p->rounding != LB_ROUND_STOCHASTIC) return LB_ERR_INVALID;
-    if (p->reserved0 != 0) return LB_ERR_INVALID;
+    if (p->tile_rows != 0 && p->tile_rows != 8 && p->tile_rows != 16) return LB_ERR_INVALID;
+    if (p->tile_rows == 16 && p->precision == LB_FP64) return LB_ERR_INVALID;
     const double vals[] = {p->tau_A, p->tau_B, p->G_A1, p->G_A2, p->G_B1, p->G_B2, p->G_X,
                            p->rho0, p->u_wall, p->init_amp, p->rho_ref, p->g_x, p->kolmo_amp,
                            p->kolmo_k};
@@ -124,22 +125,21 @@ template <typename C>
 static void fill_coef(Coef<C>& k, const lb_params* p) {
     const double Ga[2] = {p->G_A1, p->G_B1};
     const double Gr[2] = {p->G_A2, p->G_B2};
-    // d_x, d_y in {0, +-1, +-2}: the products below are exact
-    for (int r = 0; r < 12; ++r) {
-        const int c2 = rdx(r) * rdx(r) + rdy(r) * rdy(r);
+    // K(|d|^2) per species: attraction on the first belt (|d|^2 = 1, 2) with
+    // the D2Q9 weights, repulsion on both belts with the weights p; the row
+    // sums use K(1), K(2), K(5) and 2 K(4), 2 K(5), 2 K(8) (doubling is exact)
+    const int c2s[6] = {1, 2, 5, 4, 5, 8};
+    for (int r = 0; r < 6; ++r) {
+        const int c2 = c2s[r];
         C K[2];
         for (int s = 0; s < 2; ++s)
-            K[s] = (C)((r < 4 ? Ga[s] * w_weight(c2) : 0.0) + Gr[s] * p_weight(c2));
-        k.KX[r].x = K[0] * (C)rdx(r);
-        k.KX[r].y = K[1] * (C)rdx(r);
-        k.KY[r].x = K[0] * (C)rdy(r);
-        k.KY[r].y = K[1] * (C)rdy(r);
-        if (r < 4) {
-            const C w = (C)w_weight(c2);
-            k.WX[r].x = k.WX[r].y = w * (C)rdx(r);
-            k.WY[r].x = k.WY[r].y = w * (C)rdy(r);
-        }
+            K[s] = (C)((c2 <= 2 ? Ga[s] * w_weight(c2) : 0.0) + Gr[s] * p_weight(c2));
+        const C f = r < 3 ? C(1) : C(2);
+        k.KC[r].x = K[0] * f;
+        k.KC[r].y = K[1] * f;
     }
+    k.WC[0].x = k.WC[0].y = (C)w_weight(1);
+    k.WC[1].x = k.WC[1].y = (C)w_weight(2);
     // Offsets are taken from rho_ref rounded to the compute precision, so that
     // rho = rho_ref + sum_i h_i holds with the same rho_ref on every path.
     const double rref = (double)(C)(p->rho_ref > 0.0 ? p->rho_ref : p->rho0);
@@ -288,8 +288,15 @@ int choose_seg(const int* nstrips, const int* ntiles_y, int nlat, int G) {
     return best_seg;
 }
 
+int max_spt(int precision) { return precision == LB_FP64 ? 1 : 2; }
+int default_spt(int precision) { return max_spt(precision); }
+int tiles_y(const Lattice& L, int spt) {
+    const int ty = kernel_tile_y(L.p.precision) * spt;
+    return (L.p.ny + ty - 1) / ty;
+}
+
 template <typename C>
-static void fill_desc(LatDesc<C>& d, const Lattice& L, const Coef<C>& k, int wall0) {
+static void fill_desc(LatDesc<C>& d, const Lattice& L, const Coef<C>& k, int wall0, int ntiles) {
     memset(&d, 0, sizeof(d));
     for (int b = 0; b < 2; ++b) {
         d.tin[b] = L.tblock[b];
@@ -301,7 +308,7 @@ static void fill_desc(LatDesc<C>& d, const Lattice& L, const Coef<C>& k, int wal
     d.st = L.st;
     d.wall0 = wall0;
     d.nstrips = L.nstrips;
-    d.ntiles_y = L.ntiles_y;
+    d.ntiles_y = ntiles;
     d.stress_every = L.p.stress_every;
     d.stress_t0 = L.p.stress_t0;
 }
@@ -322,19 +329,23 @@ struct Item {
 // seg < 0: the tiles of all lattices in strip order (lattice, strip, tile
 // row) cut into G contiguous runs of equal estimated cost, each run cut
 // again at strip boundaries: every CTA walks one or two strips.
-void partition(Lattice* const* lats, int nlat, int seg, int sms, std::vector<Item>& items,
+void partition(Lattice* const* lats, int nlat, int seg, int spt, int sms, std::vector<Item>& items,
                std::vector<int>& cta, int* grid) {
     items.clear();
     cta.clear();
+    std::vector<int> nty((size_t)nlat);
     long long tiles = 0;
-    for (int l = 0; l < nlat; ++l) tiles += (long long)lats[l]->nstrips * lats[l]->ntiles_y;
+    for (int l = 0; l < nlat; ++l) {
+        nty[(size_t)l] = tiles_y(*lats[l], spt);
+        tiles += (long long)lats[l]->nstrips * nty[(size_t)l];
+    }
     // Tile costs measured on GB300, relative to a full interior tile: tiles
     // that write periodic ghost copies 1.26, ragged tiles 1.04, and the first
     // tile of an item one tile more (its block ring fills and it computes 12
     // deviation rows).
     auto cost = [&](int l, int sx, int ty) {
         const Lattice& L = *lats[l];
-        const int tx = kernel_tile_x(L.p.precision), tyy = kernel_tile_y(L.p.precision);
+        const int tx = kernel_tile_x(L.p.precision), tyy = kernel_tile_y(L.p.precision) * spt;
         const int x0 = sx * tx, y0 = ty * tyy;
         const bool full = x0 + tx <= L.p.nx && y0 + tyy <= L.p.ny;
         if (!full) return 1.04;
@@ -350,7 +361,7 @@ void partition(Lattice* const* lats, int nlat, int seg, int sms, std::vector<Ite
         // CTAs that draw the costlier edge segments take fewer of them.
         std::vector<Item> all;
         for (int l = 0; l < nlat; ++l) {
-            const int ns = lats[l]->nstrips, nt = lats[l]->ntiles_y;
+            const int ns = lats[l]->nstrips, nt = nty[(size_t)l];
             for (int a = 0; a < nt; a += seg)
                 for (int sx = 0; sx < ns; ++sx) all.push_back({l, sx, a, std::min(a + seg, nt)});
         }
@@ -382,7 +393,7 @@ void partition(Lattice* const* lats, int nlat, int seg, int sms, std::vector<Ite
     for (int l = 0; l < nlat; ++l)
         for (int sx = 0; sx < lats[l]->nstrips; ++sx) {
             total += kItemStart;
-            for (int ty = 0; ty < lats[l]->ntiles_y; ++ty) total += cost(l, sx, ty);
+            for (int ty = 0; ty < nty[(size_t)l]; ++ty) total += cost(l, sx, ty);
         }
     total += kItemStart * G;   // roughly one extra item start per run
     long long pos = 0;          // tiles assigned so far
@@ -397,7 +408,7 @@ void partition(Lattice* const* lats, int nlat, int seg, int sms, std::vector<Ite
         bool first = true;
         while (pos < max_end && (first || acc < target || last)) {
             // an item of at least one tile, then as many as the run's cost allows
-            const int nt = lats[l]->ntiles_y;
+            const int nt = nty[(size_t)l];
             int take = 0;
             acc += kItemStart;
             do {
@@ -432,12 +443,18 @@ static int default_seg(long long tiles, const int* ns, const int* nt, int nlat, 
 }
 
 // Host-only plan of a launch's work items (lb_plan_partition).
-lb_status plan_partition(const lb_params* ps, int nlat, int seg, int sms, int32_t* items,
-                         int32_t* nitems, int32_t* cta, int32_t* grid, int32_t* seg_used) {
+lb_status plan_partition(const lb_params* ps, int nlat, int seg, int tile_rows, int sms,
+                         int32_t* items, int32_t* nitems, int32_t* cta, int32_t* grid,
+                         int32_t* seg_used) {
     if (!ps || nlat < 1 || sms < 1 || !nitems || !grid || !seg_used) return LB_ERR_INVALID;
     std::vector<Lattice> lv((size_t)nlat);
     std::vector<Lattice*> lp((size_t)nlat);
     std::vector<int> ns((size_t)nlat), nt((size_t)nlat);
+    if (validate_params(&ps[0]) != LB_OK) return LB_ERR_INVALID;
+    const int ty8 = kernel_tile_y(ps[0].precision);
+    if (tile_rows != 0 && tile_rows != ty8 && tile_rows != 2 * ty8) return LB_ERR_INVALID;
+    const int spt = tile_rows == 0 ? 1 : tile_rows / ty8;
+    if (spt > max_spt(ps[0].precision)) return LB_ERR_INVALID;
     long long tiles = 0;
     for (int l = 0; l < nlat; ++l) {
         if (validate_params(&ps[l]) != LB_OK || ps[l].precision != ps[0].precision)
@@ -445,19 +462,19 @@ lb_status plan_partition(const lb_params* ps, int nlat, int seg, int sms, int32_
         Lattice& L = lv[(size_t)l];
         L.p = ps[l];
         L.g = make_geom(&ps[l]);
-        const int tx = kernel_tile_x(ps[l].precision), ty = kernel_tile_y(ps[l].precision);
+        const int tx = kernel_tile_x(ps[l].precision);
         L.nstrips = (ps[l].nx + tx - 1) / tx;
-        L.ntiles_y = (ps[l].ny + ty - 1) / ty;
+        L.ntiles_y = tiles_y(L, 1);
         lp[(size_t)l] = &L;
         ns[(size_t)l] = L.nstrips;
-        nt[(size_t)l] = L.ntiles_y;
-        tiles += (long long)L.nstrips * L.ntiles_y;
+        nt[(size_t)l] = tiles_y(L, spt);
+        tiles += (long long)L.nstrips * nt[(size_t)l];
     }
     const int s = seg != 0 ? seg : default_seg(tiles, ns.data(), nt.data(), nlat, sms);
     std::vector<Item> it;
     std::vector<int> c;
     int G = 0;
-    partition(lp.data(), nlat, s, sms, it, c, &G);
+    partition(lp.data(), nlat, s, spt, sms, it, c, &G);
     const int cap_items = *nitems, cap_cta = *grid;
     *nitems = (int32_t)it.size();
     *grid = G;
@@ -473,35 +490,28 @@ lb_status plan_partition(const lb_params* ps, int nlat, int seg, int sms, int32_
     return LB_OK;
 }
 
-int launch_items(Lattice* const* lats, int nlat, int seg, int sms) {
-    std::vector<Item> items;
-    std::vector<int> cta;
-    int grid = 0;
-    partition(lats, nlat, seg, sms, items, cta, &grid);
-    return (int)items.size();
-}
-
 lb_status launch_build(Launch& Ln, Lattice* const* lats, int nlat, void* descs, double* slots,
                        unsigned int* ticket, int sms, cudaStream_t stream, void* host_scratch,
-                       int forced_seg) {
+                       int forced_seg, int spt) {
     if (nlat < 1) return LB_ERR_INVALID;
     const int prec = lats[0]->p.precision;
+    if (spt < 1 || spt > max_spt(prec)) return LB_ERR_INVALID;
     std::vector<int> ns((size_t)nlat), nt((size_t)nlat);
     bool allper = true, gen = false;
     long long tiles = 0, strips = 0;
     for (int l = 0; l < nlat; ++l) {
         ns[(size_t)l] = lats[l]->nstrips;
-        nt[(size_t)l] = lats[l]->ntiles_y;
+        nt[(size_t)l] = tiles_y(*lats[l], spt);
         allper = allper && lats[l]->g.periodic;
         gen = gen || lats[l]->kd.source || lats[l]->kd.has_accel;
-        tiles += (long long)lats[l]->nstrips * lats[l]->ntiles_y;
+        tiles += (long long)lats[l]->nstrips * nt[(size_t)l];
         strips += lats[l]->nstrips;
     }
     const int seg = forced_seg != 0 ? forced_seg : default_seg(tiles, ns.data(), nt.data(), nlat, sms);
     std::vector<Item> items;
     std::vector<int> cta;
     int grid = 0;
-    partition(lats, nlat, seg, sms, items, cta, &grid);
+    partition(lats, nlat, seg, spt, sms, items, cta, &grid);
     const int nitems = (int)items.size();
     // wall item lists: per lattice, the bottom items by strip, then the top ones
     std::vector<int> wall((size_t)(2 * strips), -1), wall0((size_t)nlat);
@@ -519,9 +529,11 @@ lb_status launch_build(Launch& Ln, Lattice* const* lats, int nlat, void* descs, 
     for (int l = 0; l < nlat; ++l) {
         lats[l]->seg = seg;
         if (prec == LB_FP64)
-            fill_desc(*reinterpret_cast<LatDesc<double>*>(hs + l * dsz), *lats[l], lats[l]->kd, wall0[(size_t)l]);
+            fill_desc(*reinterpret_cast<LatDesc<double>*>(hs + l * dsz), *lats[l], lats[l]->kd,
+                      wall0[(size_t)l], nt[(size_t)l]);
         else
-            fill_desc(*reinterpret_cast<LatDesc<float>*>(hs + l * dsz), *lats[l], lats[l]->kf, wall0[(size_t)l]);
+            fill_desc(*reinterpret_cast<LatDesc<float>*>(hs + l * dsz), *lats[l], lats[l]->kf,
+                      wall0[(size_t)l], nt[(size_t)l]);
     }
     // device tables after the wall slots: items (16-byte aligned), CTA offsets, wall lists
     int4* d_items = reinterpret_cast<int4*>(slots + 2 * (size_t)nitems);
@@ -539,6 +551,7 @@ lb_status launch_build(Launch& Ln, Lattice* const* lats, int nlat, void* descs, 
     if (e != cudaSuccess) return cuda_status(e);
     Ln.precision = prec;
     Ln.variant = (allper ? 1 : 0) | (gen ? 2 : 0);
+    Ln.spt = spt;
     Ln.grid = dim3((unsigned)grid, 1, 1);
     Ln.nitems = nitems;
     Ln.seg = seg;
@@ -577,7 +590,7 @@ lb_status launch_build(Launch& Ln, Lattice* const* lats, int nlat, void* descs, 
 
 lb_status launch_run(const Launch& Ln, cudaStream_t s) {
     const void* args = Ln.precision == LB_FP64 ? (const void*)&Ln.ad : (const void*)&Ln.af;
-    return cuda_status(launch_step(Ln.precision, args, Ln.variant, Ln.grid, s));
+    return cuda_status(launch_step(Ln.precision, args, Ln.variant, Ln.spt, Ln.grid, s));
 }
 
 static lb_status lattice_observe_pull(Lattice& L, int obs, double* out, int q0, int q1, int pull,

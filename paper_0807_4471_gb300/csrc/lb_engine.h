@@ -35,6 +35,7 @@ struct Lattice {
 struct Launch {
     int precision;
     int variant;             // bit 0: all periodic; bit 1: general forcing
+    int spt;                 // sites per thread: tiles of 8 spt rows
     dim3 grid;
     int nitems, seg;
     BatchArgs<double> ad;
@@ -51,11 +52,18 @@ size_t lattice_bytes(const lb_params* p);
 lb_status lattice_setup(Lattice& L, const lb_params* p, char* region);
 
 // Host-only plan of one launch's work items (the lb_plan_partition entry).
-lb_status plan_partition(const lb_params* ps, int nlat, int seg, int sms, int32_t* items,
-                         int32_t* nitems, int32_t* cta, int32_t* grid, int32_t* seg_used);
+lb_status plan_partition(const lb_params* ps, int nlat, int seg, int tile_rows, int sms,
+                         int32_t* items, int32_t* nitems, int32_t* cta, int32_t* grid,
+                         int32_t* seg_used);
 
 // Segment length (tiles per work item) minimising the most loaded CTA.
 int choose_seg(const int* nstrips, const int* ntiles_y, int nlat, int G);
+
+// Sites per thread of the step kernel: the tile shapes a precision has
+// (tiles of 8 spt rows), the library's default, and a lattice's tile rows.
+int max_spt(int precision);
+int default_spt(int precision);
+int tiles_y(const Lattice& L, int spt);
 
 // Write the lattices' descriptors to `descs` (device, 128-byte aligned, room
 // for nlat LatDesc<double>) through `host_scratch` (as large, host) and fill
@@ -65,11 +73,10 @@ int choose_seg(const int* nstrips, const int* ntiles_y, int nlat, int G);
 // into one contiguous run per CTA.  `slots` holds launch_area_doubles(tiles,
 // strips, sms) doubles for the lattices' total tiles and strips: the per-item
 // wall slots and the item tables.
+// spt: sites per thread of the launch's kernel (1 or 2, see max_spt).
 lb_status launch_build(Launch& Ln, Lattice* const* lats, int nlat, void* descs, double* slots,
                        unsigned int* ticket, int sms, cudaStream_t stream, void* host_scratch,
-                       int seg = 0);
-// Work items of a launch over lats with segment length seg.
-int launch_items(Lattice* const* lats, int nlat, int seg, int sms);
+                       int seg = 0, int spt = 1);
 size_t launch_area_doubles(size_t tiles, size_t strips, int sms);
 lb_status launch_run(const Launch& Ln, cudaStream_t s);
 

@@ -50,30 +50,22 @@ struct Geom {
     int periodic;       // 1: periodic in y; 0: Couette walls in y
 };
 
-// One representative d of each +-d pair of the 24-neighbour stencil; the
-// first four are the first belt (also the pairs of the cross term).
-__host__ __device__ constexpr int rdx(int k) {
-    return k == 0 ? 1 : k == 1 ? 0 : k == 2 ? 1 : k == 3 ? -1 : k == 4 ? 2 : k == 5 ? 0
-         : k == 6 ? 2 : k == 7 ? 1 : k == 8 ? -1 : k == 9 ? -2 : k == 10 ? 2 : -2;
-}
-__host__ __device__ constexpr int rdy(int k) {
-    return k == 0 ? 0 : k == 1 ? 1 : k == 2 ? 1 : k == 3 ? 1 : k == 4 ? 0 : k == 5 ? 2
-         : k == 6 ? 1 : k == 7 ? 2 : k == 8 ? 2 : k == 9 ? 1 : k == 10 ? 2 : 2;
-}
-
 // The (A, B) pair type of a compute precision.
 template <typename C> struct PairOf;
 template <> struct PairOf<float> { typedef float2 T; };
 template <> struct PairOf<double> { typedef double2 T; };
 
-// Per-launch model coefficients, in the compute precision C.  Stencil
-// weights are (A, B) pairs already multiplied by the component of d, so that
-// one paired multiply-add serves both species.
+// Per-launch model coefficients, in the compute precision C.  The stencil
+// sums of Eq. (2) are taken row by row (see the step kernel): with
+// K(|d|^2) = G^a w(|d|^2) + G^r p(|d|^2) per species, the like-species
+// weights are the (A, B) pairs KC = {K(1), K(2), K(5), 2 K(4), 2 K(5),
+// 2 K(8)} (the factors 2 are the stencil components |d_x| or |d_y| = 2,
+// exact), and the cross-species ones WC = {w(1), w(2)} for both species.
 template <typename C>
 struct Coef {
     typedef typename PairOf<C>::T C2;
-    C2 KX[12], KY[12]; // like-species weights (G^a w(d) + G^r p(d)) d_x, d_y per rep d
-    C2 WX[4], WY[4];   // cross-species weights w(d) d_x, w(d) d_y (same for A and B)
+    C2 KC[6];          // like-species row weights, (A, B) pairs
+    C2 WC[2];          // cross-species row weights, equal in both lanes
     C gx_rho0;         // G_X / rho0
     C psi_ref;         // Psi(rho_ref)
     C psi_scale;       // P exp(-rho_ref / rho0)
@@ -110,7 +102,7 @@ struct alignas(128) LatDesc {
     DevStats* st;
     int wall0;             // this lattice's wall items: wall_items[wall0 .. wall0 + 2 nstrips)
     int nstrips;           // ceil(nx / TX)
-    int ntiles_y;          // ceil(ny / TY)
+    int ntiles_y;          // tile rows of the launch's tile shape
     int stress_every;
     long long stress_t0;
 };
@@ -161,12 +153,12 @@ int kernel_elem_bytes(int precision);
 int kernel_smem_obs_bytes(int precision);
 int kernel_block_rows(int precision);
 
-// obs = OBS_NONE: the persistent step kernel over `grid` CTAs; otherwise the
-// observe kernel with one CTA per tile.
 // Step: the persistent multi-lattice kernel (args: BatchArgs<C>), variant
-// bit 0 = every lattice periodic, bit 1 = general forcing.  Observe: one
-// lattice, one CTA per tile (args: StepArgs<C>, tin: tile-box load map).
-cudaError_t launch_step(int precision, const void* args, int variant, dim3 grid, cudaStream_t s);
+// bit 0 = every lattice periodic, bit 1 = general forcing, spt sites per
+// thread (tiles of 8 spt rows).  Observe: one lattice, one CTA per 8-row
+// tile (args: StepArgs<C>, tin: tile-box load map).
+cudaError_t launch_step(int precision, const void* args, int variant, int spt, dim3 grid,
+                        cudaStream_t s);
 // Opt the kernels of a precision into their shared memory (once per device;
 // call before capturing launches into a graph).
 cudaError_t kernels_configure(int precision);
@@ -187,7 +179,7 @@ cudaError_t launch_load_pops(int precision, const Geom& g, const void* coef, voi
 template <int P>
 cudaError_t configure_prec();
 template <int P>
-cudaError_t launch_step_prec(const void* args, int variant, dim3 grid, cudaStream_t s);
+cudaError_t launch_step_prec(const void* args, int variant, int spt, dim3 grid, cudaStream_t s);
 template <int P>
 cudaError_t launch_observe_prec(const CUtensorMap* tin, const void* args, dim3 grid,
                                 cudaStream_t s);

@@ -264,27 +264,155 @@ __device__ __forceinline__ void collide(const C2 h[9], C2 out[9], C2 drho, C2 rh
     }
 }
 
+// ------------------------------------------------------- force of Eq. (2)
+// The stencil sums of Eq. (2) are taken row by row.  For the stencil row at
+// vertical offset dy of a site, with the row's deviations q(dx), dx = -2..2
+// (Psi for the like-species terms, rho for the cross term), and weights
+// K(d) that depend on |d|^2 = dx^2 + dy^2 only:
+//   sum_dx K(d) d_x q(dx) = K(1,|dy|) [q(1) - q(-1)] + 2 K(2,|dy|) [q(2) - q(-2)],
+//   sum_dx K(d) d_y q(dx) = dy [K(0,|dy|) q(0) + K(1,|dy|) (q(1) + q(-1))
+//                              + K(2,|dy|) (q(2) + q(-2))].
+// (The reference values of Psi and rho drop out: sum_d K(d) d = 0.)  The
+// differences and sums of a row are shared by every site whose stencil
+// holds the row; each site adds its rows in the order dy = -2 .. 2, so a
+// site's force is the same whether it shares rows with another or not.
+
+// The shared quantities of one stencil row, p at the site's column.
+template <typename C2>
+struct Row5 {
+    C2 d1, d2, s1, s2, q0;
+};
+template <typename C2>
+__device__ __forceinline__ Row5<C2> row5(const C2* p) {
+    const C2 m2 = p[-2], m1 = p[-1], q0 = p[0], p1 = p[1], p2 = p[2];
+    Row5<C2> r;
+    r.d1 = psub(p1, m1);
+    r.d2 = psub(p2, m2);
+    r.s1 = padd(p1, m1);
+    r.s2 = padd(p2, m2);
+    r.q0 = q0;
+    return r;
+}
+template <typename C2>
+struct Row3 {
+    C2 e, t, q0;
+};
+template <typename C2>
+__device__ __forceinline__ Row3<C2> row3(const C2* p) {
+    const C2 m1 = p[-1], q0 = p[0], p1 = p[1];
+    Row3<C2> r;
+    r.e = psub(p1, m1);
+    r.t = padd(p1, m1);
+    r.q0 = q0;
+    return r;
+}
+
+// Like-species row at offset dy (|dy| <= 2) into the x and y sums, with the
+// weights KC = {K(1), K(2), K(5), 2K(4), 2K(5), 2K(8)}: x takes
+// K(1,|dy|) = K(1), K(2), K(5) and 2K(2,|dy|) = 2K(4), 2K(5), 2K(8) for
+// |dy| = 0, 1, 2; y takes {K(1), K(2), K(5)} for |dy| = 1 and
+// {2K(4), 2K(5), 2K(8)} for |dy| = 2.
+template <typename C, typename C2>
+__device__ __forceinline__ void like_row(int dy, const Row5<C2>& r, const Coef<C>& k, C2& fx,
+                                         C2& fy) {
+    const int a = dy < 0 ? -dy : dy;
+    fx = pfma(a == 0 ? k.KC[0] : (a == 1 ? k.KC[1] : k.KC[2]), r.d1, fx);
+    fx = pfma(a == 0 ? k.KC[3] : (a == 1 ? k.KC[4] : k.KC[5]), r.d2, fx);
+    if (a != 0) {
+        C2 t = pmul(a == 1 ? k.KC[0] : k.KC[3], r.q0);
+        t = pfma(a == 1 ? k.KC[1] : k.KC[4], r.s1, t);
+        t = pfma(a == 1 ? k.KC[2] : k.KC[5], r.s2, t);
+        fy = dy > 0 ? padd(fy, t) : psub(fy, t);
+    }
+}
+// Cross-species row at offset dy (|dy| <= 1), D2Q9 weights WC = {w(1), w(2)}.
+template <typename C, typename C2>
+__device__ __forceinline__ void cross_row(int dy, const Row3<C2>& r, const Coef<C>& k, C2& qx,
+                                          C2& qy) {
+    qx = pfma(dy == 0 ? k.WC[0] : k.WC[1], r.e, qx);
+    if (dy != 0) {
+        C2 u = pmul(k.WC[0], r.q0);
+        u = pfma(k.WC[1], r.t, u);
+        qy = dy > 0 ? padd(qy, u) : psub(qy, u);
+    }
+}
+
+// Stencil sums of NS vertically adjacent sites.  ps, rr: the Psi and rho
+// deviation rows (row stride RXS) at the sites' column, starting two rows
+// above the first site.  Out, per site s: fx, fy = sum_d K_s(d) d Psi_s(r+d),
+// qx, qy = sum_d w(d) d rho_s(r+d) (species not yet swapped), and the site's
+// own Psi and rho deviations.
+template <int NS, int RXS, typename C, typename C2>
+__device__ __forceinline__ void force_sums(const C2* ps, const C2* rr, const Coef<C>& k, C2 fx[NS],
+                                           C2 fy[NS], C2 qx[NS], C2 qy[NS], C2 dpsi[NS],
+                                           C2 drho[NS]) {
+    const C2 z = pset(C(0));
+#pragma unroll
+    for (int s = 0; s < NS; ++s) fx[s] = fy[s] = qx[s] = qy[s] = z;
+#pragma unroll
+    for (int r = 0; r < NS + 4; ++r) {
+        const Row5<C2> w = row5(ps + r * RXS);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const int dy = r - 2 - s;
+            if (dy >= -2 && dy <= 2) like_row(dy, w, k, fx[s], fy[s]);
+            if (dy == 0) dpsi[s] = w.q0;
+        }
+    }
+#pragma unroll
+    for (int r = 1; r < NS + 3; ++r) {
+        const Row3<C2> w = row3(rr + r * RXS);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const int dy = r - 2 - s;
+            if (dy >= -1 && dy <= 1) cross_row(dy, w, k, qx[s], qy[s]);
+            if (dy == 0) drho[s] = w.q0;
+        }
+    }
+}
+
+// Plain global stores of a stored pair, with an L2 cache policy.
+__device__ __forceinline__ void st_pair(float2* p, float2 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y),
+                 "l"(pol));
+}
+__device__ __forceinline__ void st_pair(double2* p, double2 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(v.x), "d"(v.y),
+                 "l"(pol));
+}
+template <typename T2>
+__device__ __forceinline__ void st_pair(T2* p, T2 v, uint64_t pol) {   // 16-bit pairs
+    static_assert(sizeof(T2) == 4, "a pair of 16-bit values");
+    asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(p),
+                 "r"(*reinterpret_cast<const uint32_t*>(&v)), "l"(pol));
+}
+
 // Where a site update sends its result.
+enum SiteSink : int { SINK_STAGE = 0, SINK_GLOBAL = 1 };
 template <typename T2>
 struct SiteOut {
-    T2* stage;             // staging tile slot of the site (step kernel)
+    T2* stage;             // SINK_STAGE: staging tile slot of the site (plane 0)
+    T2* gout;              // SINK_GLOBAL: the site's pair in plane 0 of the output buffer
+    long long plane;       // SINK_GLOBAL: plane stride (pairs)
+    long long gdy;         // SINK_GLOBAL: offset of the periodic image in y (0: none)
+    int gdx;               // SINK_GLOBAL: offset of the periodic image in x (0: none)
+    uint64_t pol;          // SINK_GLOBAL: L2 policy of the stores
     uint32_t key;          // stochastic rounding: hash of the lattice's step
     int obs;               // ObsKind (observe kernel) or OBS_NONE
     double* obs_out;
     int q0, q1;
 };
 
-// One lattice site: moments, the force of Eq. (2) from the staged deviation
-// rows, and either the forced BGK collision and write-back (OBS = false) or
-// the observables (OBS = true).  ps[k] / rr[k]: Psi / rho deviation rows
-// y + k - 2, pointing at the site's column; rr[2][0] holds the site's own
-// density deviations, summed from the same populations.  Both species are
+// One lattice site, given its force sums: moments from its pulled
+// populations, the force of Eq. (2), and either the forced BGK collision and
+// write-back (OBS = false) or the observables (OBS = true).  Both species are
 // carried as (A, B) pairs throughout.
-template <int P, bool OBS, bool GEN, int PS>
+template <int P, bool OBS, bool GEN, int PS, int SINK>
 __device__ __forceinline__ void site_update(
     const typename Prec<P>::T2* bm, const typename Prec<P>::T2* b0,
-    const typename Prec<P>::T2* bp, const typename Prec<P>::C2* const ps[5],
-    const typename Prec<P>::C2* const rr[5], int x, int y, bool per, int pull, const Geom& g,
+    const typename Prec<P>::T2* bp, typename Prec<P>::C2 fxl, typename Prec<P>::C2 fyl,
+    typename Prec<P>::C2 qx, typename Prec<P>::C2 qy, typename Prec<P>::C2 dpsi,
+    typename Prec<P>::C2 drho, int x, int y, bool per, int pull, const Geom& g,
     const LatVals<typename Prec<P>::C>& v, const Coef<typename Prec<P>::C>& k,
     const SiteOut<typename Prec<P>::T2>& o, double red[4], bool& bad) {
     typedef typename Prec<P>::T2 T2;
@@ -292,7 +420,6 @@ __device__ __forceinline__ void site_update(
     typedef typename Prec<P>::C2 C2;
     C2 h[9];
     load_site<P, PS>(bm, b0, bp, y, per, pull, g, v, h);
-    const C2 drho = rr[2][0];
     const C2 rho = padd(pset(v.rho_ref), drho);
     // sum_i w_i c_i = 0, so the offsets carry all of j
     const C2 d57 = psub(h[5], h[7]), d68 = psub(h[6], h[8]);
@@ -304,34 +431,13 @@ __device__ __forceinline__ void site_update(
     }
     if (!(isfinite(rho.x) && isfinite(rho.y))) bad = true;
 
-    // Eq. (2): F_s = -Psi_s(r) sum_d K_s(d) d [Psi_s(r+d) - Psi_s(r-d)]
-    //               - (G_X/rho0) rho_s(r) sum_d w(d) d [rho_s'(r+d) - rho_s'(r-d)]
-    // over one representative d of each +-d pair (the reference values cancel
-    // in the differences); belt-1 and belt-2 pairs accumulate separately.
-    C2 ax1 = pset(C(0)), ay1 = pset(C(0)), ax2 = pset(C(0)), ay2 = pset(C(0));
-#pragma unroll
-    for (int q = 0; q < 12; ++q) {
-        const int dx = rdx(q), dy = rdy(q);
-        const C2 dp = psub(ps[2 + dy][dx], ps[2 - dy][-dx]);
-        C2& ax = q < 4 ? ax1 : ax2;
-        C2& ay = q < 4 ? ay1 : ay2;
-        if (dx != 0) ax = pfma(k.KX[q], dp, ax);
-        if (dy != 0) ay = pfma(k.KY[q], dp, ay);
-    }
-    // cross term: (sum w d_x [rho_A(r+d) - rho_A(r-d)], same for B); species
-    // A feels rho_B, so the pair is used swapped
-    C2 qx = pset(C(0)), qy = pset(C(0));
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int dx = rdx(q), dy = rdy(q);
-        const C2 dr = psub(rr[2 + dy][dx], rr[2 - dy][-dx]);
-        if (dx != 0) qx = pfma(k.WX[q], dr, qx);
-        if (dy != 0) qy = pfma(k.WY[q], dr, qy);
-    }
-    const C2 npc = psub(pset(-v.psi_ref), ps[2][0]);      // -Psi_s(r)
+    // Eq. (2): F_s = -Psi_s(r) sum_d K_s(d) d Psi_s(r + d)
+    //               - (G_X/rho0) rho_s(r) sum_d w(d) d rho_s'(r + d);
+    // species A feels rho_B, so the cross sums are used swapped.
+    const C2 npc = psub(pset(-v.psi_ref), dpsi);          // -Psi_s(r)
     const C2 ng = pmul(pset(-v.gx_rho0), rho);             // -(G_X/rho0) rho_s
-    C2 Fx = pfma(npc, padd(ax1, ax2), pmul(ng, pair(qx.y, qx.x)));
-    C2 Fy = pfma(npc, padd(ay1, ay2), pmul(ng, pair(qy.y, qy.x)));
+    C2 Fx = pfma(npc, fxl, pmul(ng, pair(qx.y, qx.x)));
+    C2 Fy = pfma(npc, fyl, pmul(ng, pair(qy.y, qy.x)));
     if (GEN && k.has_accel) {
         C acc = k.g_x;
         if (k.kolmo_amp != C(0)) acc += k.kolmo_amp * csin(v.kolmo_w * C(y));
@@ -402,12 +508,31 @@ __device__ __forceinline__ void site_update(
         for (int i = 0; i < 9; ++i) e[i] = enc2<T2, C>(hs[i].x, hs[i].y);
     }
 
-    // Every tile goes through the staging tile and leaves it by a bulk tensor
-    // store (clipped at the lattice edge); the periodic ghost copies follow
-    // by the plain stores of write_edges after the tile's barrier.
-    constexpr int TX = Prec<P>::TX, TY = Prec<P>::TY;
+    if constexpr (SINK == SINK_STAGE) {
+        // The staging tile leaves by a bulk tensor store (clipped at the
+        // lattice edge); the periodic ghost copies follow by the plain
+        // stores of write_edges after the tile's barrier.
+        constexpr int TX = Prec<P>::TX, TY = Prec<P>::TY;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) o.stage[i * TY * TX] = e[i];
+        for (int i = 0; i < 9; ++i) o.stage[i * TY * TX] = e[i];
+    } else {
+        // Straight to the output buffer, and to the periodic images of a
+        // site within three sites of an edge (ghost columns, and ghost rows
+        // when periodic in y).
+#pragma unroll
+        for (int i = 0; i < 9; ++i) st_pair(o.gout + i * o.plane, e[i], o.pol);
+        if (o.gdx != 0 || o.gdy != 0) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                T2* d = o.gout + i * o.plane;
+                if (o.gdx) st_pair(d + o.gdx, e[i], o.pol);
+                if (o.gdy) {
+                    st_pair(d + o.gdy, e[i], o.pol);
+                    if (o.gdx) st_pair(d + o.gdy + o.gdx, e[i], o.pol);
+                }
+            }
+        }
+    }
     if (!per && (y == 0 || y == g.ny - 1)) {
         // x-momentum handed to the wall by the links that will bounce back
         // at the next streaming: c_x (f*_i + f_opp), f_opp = f*_i - 6 w_i
@@ -509,26 +634,29 @@ __device__ __forceinline__ void block_sum4(double red[4], double (*s_red)[4]) {
 
 // ------------------------------------------------------------ step kernel
 // Persistent and multi-lattice.  The work items of a launch are runs of
-// tiles (TY rows each) down TX-wide column strips, over all lattices; CTA b
-// takes the items a.items[a.cta_items[b] .. a.cta_items[b + 1]) of a table
-// the host builds (segments dealt by estimated work in band order, or one
-// contiguous run per CTA).  Walking down a strip, a CTA keeps the 8-row
-// blocks of f* (TMA-loaded into a ring of NB slots, ahead of use and across
-// item boundaries) and a window of the density/Psi deviation rows
-// y0 - 2 .. y0 + 9 of the current tile, whose last four rows are carried
-// forward as the next tile's first four; so each block is loaded and each
-// deviation row computed once per strip, and only the x halo (4 of 64
-// columns) is redundant.  Every thread keeps one column and row of the
-// window in both phases, so all its shared-memory addresses are fixed.
-// Tiles leave through a staging tile by TMA bulk tensor stores, clipped at
-// the lattice edge; tiles near an edge then write the periodic ghost copies.
-// The last CTA to finish advances every lattice's step counter and buffer
+// tiles (TY = 8 SPT rows each) down TX-wide column strips, over all
+// lattices; CTA b takes the items a.items[a.cta_items[b] .. a.cta_items[b + 1])
+// of a table the host builds (segments dealt by estimated work in band
+// order, or one contiguous run per CTA).  Walking down a strip, a CTA keeps
+// the 8-row blocks of f* (TMA-loaded into a ring of NB slots, ahead of use
+// and across item boundaries) and a window of the density/Psi deviation rows
+// y0 - 2 .. y0 + TY + 1 of the current tile, whose last four rows are
+// carried forward as the next tile's first four; so each block is loaded
+// and each deviation row computed once per strip, and only the x halo (4 of
+// 64 columns) is redundant.  Every thread keeps one column and SPT rows of
+// the window in both phases, so all its shared-memory addresses within a
+// slot are fixed.  SPT = 1: tiles leave through a staging tile by TMA bulk
+// tensor stores, clipped at the lattice edge, and tiles near an edge then
+// write the periodic ghost copies.  SPT = 2: each thread updates two
+// vertically adjacent sites, which share four of their six stencil rows,
+// and stores them (with their ghost copies) to global memory itself.  The
+// last CTA to finish advances every lattice's step counter and buffer
 // parity and takes the Couette wall samples.
 // V: bit 0 = every lattice periodic (no wall code); bit 1 = general forcing.
-template <int P, int V>
-__global__ void __launch_bounds__(Layout<P>::NT, 1)
+template <int P, int V, int SPT>
+__global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
     k_step(const __grid_constant__ BatchArgs<typename Prec<P>::C> a) {
-    typedef Layout<P> L;
+    typedef Layout<P, SPT> L;
     typedef typename L::T2 T2;
     typedef typename L::C C;
     typedef typename L::C2 C2;
@@ -541,7 +669,7 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
     unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     C2* win_r = reinterpret_cast<C2*>(smem + L::WIN_OFF);     // [WIN][RX]
     C2* win_p = win_r + L::WIN * L::RX;                       // [WIN][RX]
-    T2* stage = reinterpret_cast<T2*>(smem + L::STAGE_OFF);   // [9][TY][TX]
+    T2* stage = reinterpret_cast<T2*>(smem + L::STAGE_OFF);   // [9][TY][TX] (SPT = 1)
     __shared__ __align__(8) uint64_t bars[L::NB];
     __shared__ int s_fail, s_last;
     __shared__ double s_red[L::NT / 32][4];
@@ -551,7 +679,7 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
     const int tid = threadIdx.x;
     const int G = gridDim.x;
     // thread 0 issues the block loads; this thread (warp 1) the bulk stores
-    // of the staging tile and the waits on them
+    // of the staging tile and the waits on them (SPT = 1)
     constexpr int kStoreThread = 32;
     // When one buffer of every lattice of the launch fits in L2 together, the
     // step's output stays there for the next step (evict last) and the input,
@@ -559,9 +687,9 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
     // The two policies are made once, by thread 0, and kept in shared memory
     // (held in registers through the tile loop, or made at each issue, they
     // cost the large lattices 1-3 %).
-    // window column and tile row of this thread (both phases)
+    // window column and block row of this thread (both phases)
     const int t_lx = tid % L::RX, t_j = tid / L::RX;
-    static_assert(L::NT == L::RX * L::TY && L::TY >= 4, "one window cell per thread and row");
+    static_assert(L::NT == L::RX * L::TYB && L::TY >= 4, "one window column per thread and block row");
     auto slot = [&](int pos) { return reinterpret_cast<T2*>(smem + (pos % L::NB) * L::SLOT_BYTES); };
     const int it_end = a.cta_items[blockIdx.x + 1];
 
@@ -581,8 +709,8 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
     griddep_launch_dependents();
 
     // Producer (thread 0): the blocks of this CTA's items, in order.  Item
-    // tiles [ty_a, ty_b) need blocks ty_a .. ty_b (block j = padded rows
-    // [8j, 8j + 8)); consecutive items' blocks follow each other.
+    // tiles [ty_a, ty_b) need blocks SPT ty_a .. SPT ty_b (block j = padded
+    // rows [8j, 8j + 8)); consecutive items' blocks follow each other.
     int p_item = a.cta_items[blockIdx.x], p_j = 0, p_pos = 0;
     // cached geometry of the producer's current item
     const CUtensorMap* p_map = nullptr;
@@ -593,7 +721,7 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
         const LatDesc<C>* d = &a.lat[w.x];
         p_x0 = w.y * L::TX;
         p_ty_a = w.z;
-        p_nblk = w.w - w.z + 1;
+        p_nblk = SPT * (w.w - w.z) + 1;
         p_map = &d->tin[*((volatile int*)&d->st->cur)];
     };
     auto issue_next = [&]() -> bool {
@@ -601,7 +729,8 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
         uint64_t* bar = &bars[p_pos % L::NB];
         mbar_expect_tx(bar, (uint32_t)L::SLOT_BYTES);
         // box origin: pair column x0 (= x0 - gx + gx) -> element 2 x0; padded row 8j
-        tma_load_3d_hint(slot(p_pos), p_map, 2 * p_x0, L::TYB * (p_ty_a + p_j), 0, bar, s_pol[0]);
+        tma_load_3d_hint(slot(p_pos), p_map, 2 * p_x0, L::TYB * (SPT * p_ty_a + p_j), 0, bar,
+                         s_pol[0]);
         ++p_pos;
         if (++p_j == p_nblk) {
             p_j = 0;
@@ -632,53 +761,59 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
         T2* fout = reinterpret_cast<T2*>(d->fbuf[cur ^ 1]);
         double wall[2] = {0.0, 0.0};
         for (int ty = ty_a; ty < ty_b; ++ty) {
-            const int q = c_pos + (ty - ty_a);   // this tile uses blocks q and q + 1
+            const int q = c_pos + SPT * (ty - ty_a);   // this tile uses blocks q .. q + SPT
             // each thread sees the blocks land itself; a timeout is acted on
             // after the next barrier (garbage read meanwhile is harmless)
-            if (!mbar_wait_bounded(&bars[q % L::NB], (q / L::NB) & 1) ||
-                !mbar_wait_bounded(&bars[(q + 1) % L::NB], ((q + 1) / L::NB) & 1))
-                s_fail = 1;
+#pragma unroll
+            for (int b = 0; b <= SPT; ++b)
+                if (!mbar_wait_bounded(&bars[(q + b) % L::NB], ((q + b) / L::NB) & 1)) s_fail = 1;
             const int y0 = ty * L::TY;
-            // The tile's padded rows [8 ty, 8 ty + 16) are blocks q (slot s0) and
-            // q + 1 (slot s1); brow(r, c): row 8 ty + r, pair column c, plane 0.
+            // The tile's padded rows [y0, y0 + 8 (SPT + 1)) are blocks q ..
+            // q + SPT; brow(r, c): padded row y0 + r, pair column c, plane 0.
             const T2* s0 = slot(q);
             const T2* s1 = slot(q + 1);
+            const T2* s2 = SPT > 1 ? slot(q + 2) : s1;
             auto brow = [&](int r, int c) {
-                return (r < L::TYB ? s0 + r * L::BX : s1 + (r - L::TYB) * L::BX) + c;
+                const T2* base = r < L::TYB ? s0 : (SPT == 1 || r < 2 * L::TYB ? s1 : s2);
+                return base + (r & (L::TYB - 1)) * L::BX + c;
             };
 
             // Phase 2: window row k holds lattice row y0 - 2 + k (padded row
-            // 8 ty + 1 + k).  Rows 4 .. TY + 3 are new: thread row t_j computes
-            // row 4 + t_j.  Rows 0 .. 3 are the previous tile's rows TY .. TY + 3,
-            // carried forward by the threads that own those (t_j >= TY - 4)
-            // before they overwrite them, or at an item's first tile computed
-            // from block q.  No other thread touches these cells in this phase.
+            // y0 + 1 + k).  Rows 4 .. TY + 3 are new: thread row t_j computes
+            // rows 4 + SPT t_j + c, c < SPT.  Rows 0 .. 3 are the previous
+            // tile's rows TY .. TY + 3, carried forward by the threads that
+            // own those before they overwrite them, or at an item's first
+            // tile computed from block q.  No other thread touches these
+            // cells in this phase.
             {
                 const int bc = t_lx - 2 + L::GX;   // pair column in the block
-                if (t_j >= L::TY - 4) {
-                    const int k = t_j - (L::TY - 4);
-                    if (ty == ty_a) {
-                        const int y = y0 - 2 + k;
-                        if (per || (y >= 0 && y < g.ny)) {
-                            C2 r, p;
-                            cell_dev<P, PS>(brow(k, bc), brow(k + 1, bc), brow(k + 2, bc), y, per,
-                                            pull, g, v, r, p);
-                            win_r[k * L::RX + t_lx] = r;
-                            win_p[k * L::RX + t_lx] = p;
+#pragma unroll
+                for (int c = 0; c < SPT; ++c) {
+                    const int k = 4 + SPT * t_j + c;
+                    const int kk = k - L::TY;
+                    if (kk >= 0) {
+                        if (ty == ty_a) {
+                            const int y = y0 - 2 + kk;
+                            if (per || (y >= 0 && y < g.ny)) {
+                                C2 r, p;
+                                cell_dev<P, PS>(brow(kk, bc), brow(kk + 1, bc), brow(kk + 2, bc), y,
+                                                per, pull, g, v, r, p);
+                                win_r[kk * L::RX + t_lx] = r;
+                                win_p[kk * L::RX + t_lx] = p;
+                            }
+                        } else {
+                            win_r[kk * L::RX + t_lx] = win_r[k * L::RX + t_lx];
+                            win_p[kk * L::RX + t_lx] = win_p[k * L::RX + t_lx];
                         }
-                    } else {
-                        win_r[k * L::RX + t_lx] = win_r[(L::TY + k) * L::RX + t_lx];
-                        win_p[k * L::RX + t_lx] = win_p[(L::TY + k) * L::RX + t_lx];
                     }
-                }
-                const int k = 4 + t_j;
-                const int y = y0 + 2 + t_j;
-                if (per || y < g.ny) {
-                    C2 r, p;
-                    cell_dev<P, PS>(brow(k, bc), brow(k + 1, bc), brow(k + 2, bc), y, per, pull, g,
-                                    v, r, p);
-                    win_r[k * L::RX + t_lx] = r;
-                    win_p[k * L::RX + t_lx] = p;
+                    const int y = y0 - 2 + k;
+                    if (per || y < g.ny) {
+                        C2 r, p;
+                        cell_dev<P, PS>(brow(k, bc), brow(k + 1, bc), brow(k + 2, bc), y, per, pull,
+                                        g, v, r, p);
+                        win_r[k * L::RX + t_lx] = r;
+                        win_p[k * L::RX + t_lx] = p;
+                    }
                 }
             }
             // mirror the deviations about the halfway walls, in the tiles whose
@@ -697,65 +832,101 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
                     win_p[k * L::RX + lx] = win_p[km * L::RX + lx];
                 }
             }
-            if (tid == kStoreThread) bulk_wait_read();   // previous bulk store has read the staging tile
+            if (SPT == 1 && tid == kStoreThread) bulk_wait_read();   // previous bulk store has read the staging tile
             __syncthreads();
             if (s_fail) break;
 
-            // Phase 3: one site per thread (lx < TX): site (x0 + t_lx, y0 + t_j),
-            // whose rows y - 2 .. y + 2 are window rows t_j .. t_j + 4 and whose
-            // populations sit in padded rows 8 ty + 2 + t_j .. 8 ty + 4 + t_j.
-            // only tiles within 3 sites of an edge write periodic ghost copies
-            const bool edge = x0 < 3 || x0 + L::TX > g.nx - 3 ||
-                              (per && (y0 < 3 || y0 + L::TY > g.ny - 3));
-            {
+            // Phase 3: SPT sites per thread (lx < TX): sites (x0 + t_lx,
+            // y0 + SPT t_j + s), whose stencil rows y - 2 .. y + 2 are window
+            // rows SPT t_j + s .. SPT t_j + s + 4 and whose populations sit in
+            // padded rows y0 + SPT t_j + s + 2 .. + 4.
+            if constexpr (SPT == 1) {
                 const int lx = t_lx, ly = t_j;
                 const int x = x0 + lx, y = y0 + ly;
                 if (lx < L::TX && x < g.nx && y < g.ny) {
                     const int bc = lx + L::GX;
-                    const C2* ps[5];
-                    const C2* rr[5];
-#pragma unroll
-                    for (int k2 = 0; k2 < 5; ++k2) {
-                        ps[k2] = win_p + (ly + k2) * L::RX + lx + 2;
-                        rr[k2] = win_r + (ly + k2) * L::RX + lx + 2;
-                    }
+                    C2 fx[1], fy[1], qx[1], qy[1], dp[1], dr[1];
+                    force_sums<1, L::RX>(win_p + ly * L::RX + lx + 2, win_r + ly * L::RX + lx + 2,
+                                         a.k, fx, fy, qx, qy, dp, dr);
                     SiteOut<T2> o;
                     o.stage = stage + ly * L::TX + lx;
                     o.key = key;
                     o.obs = OBS_NONE;
                     double wr[4] = {0.0, 0.0, 0.0, 0.0};
-                    site_update<P, false, GEN, PS>(brow(ly + 2, bc), brow(ly + 3, bc), brow(ly + 4, bc),
-                                                   ps, rr, x, y, per, pull, g, v, a.k, o, wr, bad);
+                    site_update<P, false, GEN, PS, SINK_STAGE>(
+                        brow(ly + 2, bc), brow(ly + 3, bc), brow(ly + 4, bc), fx[0], fy[0], qx[0],
+                        qy[0], dp[0], dr[0], x, y, per, pull, g, v, a.k, o, wr, bad);
                     if (!per && (y == 0 || y == g.ny - 1)) {   // FP64: wall rows only
                         wall[0] += wr[0];
                         wall[1] += wr[1];
                     }
                     fence_proxy_async();   // staging writes before the bulk store
                 }
+            } else {
+                const int lx = t_lx, ly = SPT * t_j;
+                const int x = x0 + lx, y = y0 + ly;
+                if (lx < L::TX && x < g.nx && y < g.ny) {
+                    const int bc = lx + L::GX;
+                    C2 fx[SPT], fy[SPT], qx[SPT], qy[SPT], dp[SPT], dr[SPT];
+                    force_sums<SPT, L::RX>(win_p + ly * L::RX + lx + 2,
+                                           win_r + ly * L::RX + lx + 2, a.k, fx, fy, qx, qy, dp, dr);
+                    SiteOut<T2> o;
+                    o.plane = g.plane;
+                    o.gdx = x < 3 ? g.nx : (x >= g.nx - 3 ? -g.nx : 0);
+                    o.pol = s_pol[1];
+                    o.key = key;
+                    o.obs = OBS_NONE;
+#pragma unroll
+                    for (int s = 0; s < SPT; ++s) {
+                        const int ys = y + s;
+                        if (s > 0 && ys >= g.ny) break;
+                        o.gout = fout + (long long)(ys + kGY) * g.pitch + (x + g.gx);
+                        o.gdy = !per ? 0
+                                : ys < 3 ? (long long)g.ny * g.pitch
+                                : (ys >= g.ny - 3 ? -(long long)g.ny * g.pitch : 0);
+                        double wr[4] = {0.0, 0.0, 0.0, 0.0};
+                        site_update<P, false, GEN, PS, SINK_GLOBAL>(
+                            brow(ly + s + 2, bc), brow(ly + s + 3, bc), brow(ly + s + 4, bc), fx[s],
+                            fy[s], qx[s], qy[s], dp[s], dr[s], x, ys, per, pull, g, v, a.k, o, wr,
+                            bad);
+                        if (!per && (ys == 0 || ys == g.ny - 1)) {   // FP64: wall rows only
+                            wall[0] += wr[0];
+                            wall[1] += wr[1];
+                        }
+                    }
+                }
             }
             __syncthreads();
-            // The bulk store and the next loads are issued by two threads of
-            // different warps, side by side.
-            if (tid == kStoreThread) {
-                // site (x0, y0) in padded coordinates: pair column x0 + gx, row
-                // y0 + kGY; a ragged tile's store is clipped at x = nx, y = ny
-                tma_store_3d_hint(&d->tout[cur ^ 1], stage, 2 * (x0 + L::GX), y0 + kGY, 0, s_pol[1]);
-                bulk_commit();
+            if constexpr (SPT == 1) {
+                // The bulk store and the next loads are issued by two threads
+                // of different warps, side by side.
+                if (tid == kStoreThread) {
+                    // site (x0, y0) in padded coordinates: pair column x0 + gx,
+                    // row y0 + kGY; a ragged tile's store is clipped at x = nx, y = ny
+                    tma_store_3d_hint(&d->tout[cur ^ 1], stage, 2 * (x0 + L::GX), y0 + kGY, 0,
+                                      s_pol[1]);
+                    bulk_commit();
+                }
             }
             if (tid == 0) {
                 // blocks before the next tile's first block are free
-                const int released = (ty + 1 < ty_b) ? q + 1 : q + 2;
+                const int released = (ty + 1 < ty_b) ? q + SPT : q + SPT + 1;
                 fence_proxy_async();   // generic reads of freed slots before async writes
                 while (p_pos < released + L::NB && issue_next()) {}
             }
-            if (edge) write_edges<P, L::NT>(stage, fout, g, x0, y0, per, tid);
+            if constexpr (SPT == 1) {
+                // only tiles within 3 sites of an edge write periodic ghost copies
+                const bool edge = x0 < 3 || x0 + L::TX > g.nx - 3 ||
+                                  (per && (y0 < 3 || y0 + L::TY > g.ny - 3));
+                if (edge) write_edges<P, L::NT>(stage, fout, g, x0, y0, per, tid);
+            }
         }
         if (bad) {   // a density of this lattice went non-finite
             atomicOr(&d->st->err, ERR_NONFINITE);
             bad = false;
         }
         if (s_fail) break;
-        c_pos += (ty_b - ty_a) + 1;
+        c_pos += SPT * (ty_b - ty_a) + 1;
         if (!per && (ty_a == 0 || ty_b == d->ntiles_y)) {
             // Wall momentum of an item holding a wall row (only these items'
             // slots are read), in FP64.  FP64 issues at a small fraction of
@@ -786,7 +957,7 @@ __global__ void __launch_bounds__(Layout<P>::NT, 1)
             }
         }
     }
-    if (tid == kStoreThread) bulk_wait_all();
+    if (SPT == 1 && tid == kStoreThread) bulk_wait_all();
     if (s_fail && tid == 0) {
         // Let copies in flight land before the CTA exits.  No slot is
         // re-armed once a wait has failed, so the last NB positions issued
@@ -910,13 +1081,9 @@ __global__ void __launch_bounds__(Layout<P>::NT)
         const int x = x0 + lx, y = y0 + ly;
         if (lx < L::TX && x < g.nx && y < g.ny) {
             const T2* b0 = box + (ly + kGY) * L::BX + lx + L::GX;
-            const C2* ps[5];
-            const C2* rr[5];
-#pragma unroll
-            for (int k2 = 0; k2 < 5; ++k2) {
-                ps[k2] = spsi + (ly + k2) * L::RX + lx + 2;
-                rr[k2] = srho + (ly + k2) * L::RX + lx + 2;
-            }
+            C2 fx[1], fy[1], qx[1], qy[1], dp[1], dr[1];
+            force_sums<1, L::RX>(spsi + ly * L::RX + lx + 2, srho + ly * L::RX + lx + 2, a.k, fx, fy,
+                                 qx, qy, dp, dr);
             SiteOut<T2> o;
             o.stage = nullptr;
             o.key = 0u;
@@ -924,8 +1091,9 @@ __global__ void __launch_bounds__(Layout<P>::NT)
             o.obs_out = a.obs_out;
             o.q0 = a.q0;
             o.q1 = a.q1;
-            site_update<P, true, GEN, PS>(b0 - L::BX, b0, b0 + L::BX, ps, rr, x, y, per, a.pull, g,
-                                          v, a.k, o, red, bad);
+            site_update<P, true, GEN, PS, SINK_STAGE>(b0 - L::BX, b0, b0 + L::BX, fx[0], fy[0], qx[0],
+                                                      qy[0], dp[0], dr[0], x, y, per, a.pull, g, v,
+                                                      a.k, o, red, bad);
         }
     } else if (tid == 0) {
         atomicOr(&a.st->err, ERR_TIMEOUT);
@@ -1062,12 +1230,28 @@ __global__ void k_wait_selftest(unsigned int* err, int limit) {
 #endif
 
 // ------------------------------------------------------------- launchers
-template <int P, typename KS, typename KO>
-static cudaError_t configure(KS ks, KO ko) {
+// Step kernels of precision P (8-row tiles; 16-row tiles where the
+// precision has them) and the observe kernels, variant by variant.
+template <int P>
+static cudaError_t configure_all() {
     typedef Layout<P> L;
-    cudaError_t e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ko, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM_OBS);
+    cudaError_t e = cudaSuccess;
+    auto opt = [&](auto kern, int bytes) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    };
+    opt(k_step<P, 0, 1>, L::SMEM);
+    opt(k_step<P, 1, 1>, L::SMEM);
+    opt(k_step<P, 2, 1>, L::SMEM);
+    opt(k_step<P, 3, 1>, L::SMEM);
+    if constexpr (Prec<P>::NB2 > 0) {
+        typedef Layout<P, 2> L2;
+        opt(k_step<P, 0, 2>, L2::SMEM);
+        opt(k_step<P, 1, 2>, L2::SMEM);
+        opt(k_step<P, 2, 2>, L2::SMEM);
+        opt(k_step<P, 3, 2>, L2::SMEM);
+    }
+    opt(k_observe<P, 2>, L::SMEM_OBS);
+    opt(k_observe<P, 3>, L::SMEM_OBS);
     return e;
 }
 
@@ -1079,10 +1263,7 @@ static cudaError_t ensure_configured() {
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && configured[dev]) return cudaSuccess;
-    cudaError_t e = configure<P>(k_step<P, 0>, k_observe<P, 2>);
-    if (e == cudaSuccess) e = configure<P>(k_step<P, 1>, k_observe<P, 3>);
-    if (e == cudaSuccess) e = configure<P>(k_step<P, 2>, k_observe<P, 2>);
-    if (e == cudaSuccess) e = configure<P>(k_step<P, 3>, k_observe<P, 3>);
+    cudaError_t e = configure_all<P>();
     if (e == cudaSuccess && dev >= 0 && dev < 64) configured[dev] = 1;
     return e;
 }
@@ -1097,13 +1278,10 @@ static bool pdl_enabled() {
     return on;
 }
 
-template <int P>
-cudaError_t launch_step_prec(const void* args, int variant, dim3 grid, cudaStream_t s) {
-    typedef Layout<P> L;
-    typedef typename L::C C;
-    cudaError_t e = ensure_configured<P>();
-    if (e != cudaSuccess) return e;
-    const BatchArgs<C>& a = *reinterpret_cast<const BatchArgs<C>*>(args);
+template <int P, int SPT>
+static cudaError_t launch_step_shape(const BatchArgs<typename Prec<P>::C>& a, int variant, dim3 grid,
+                                     cudaStream_t s) {
+    typedef Layout<P, SPT> L;
     // Consecutive steps on a stream overlap the next launch's set-up with the
     // previous launch's last CTAs (programmatic stream serialization); the
     // kernel waits for the previous grid before it reads the lattice state.
@@ -1117,13 +1295,26 @@ cudaError_t launch_step_prec(const void* args, int variant, dim3 grid, cudaStrea
     cfg.stream = s;
     cfg.attrs = at;
     cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    cudaError_t e;
     switch (variant & 3) {
-        case 0: e = cudaLaunchKernelEx(&cfg, k_step<P, 0>, a); break;
-        case 1: e = cudaLaunchKernelEx(&cfg, k_step<P, 1>, a); break;
-        case 2: e = cudaLaunchKernelEx(&cfg, k_step<P, 2>, a); break;
-        default: e = cudaLaunchKernelEx(&cfg, k_step<P, 3>, a); break;
+        case 0: e = cudaLaunchKernelEx(&cfg, k_step<P, 0, SPT>, a); break;
+        case 1: e = cudaLaunchKernelEx(&cfg, k_step<P, 1, SPT>, a); break;
+        case 2: e = cudaLaunchKernelEx(&cfg, k_step<P, 2, SPT>, a); break;
+        default: e = cudaLaunchKernelEx(&cfg, k_step<P, 3, SPT>, a); break;
     }
     return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_step_prec(const void* args, int variant, int spt, dim3 grid, cudaStream_t s) {
+    typedef typename Prec<P>::C C;
+    cudaError_t e = ensure_configured<P>();
+    if (e != cudaSuccess) return e;
+    const BatchArgs<C>& a = *reinterpret_cast<const BatchArgs<C>*>(args);
+    if (spt == 1) return launch_step_shape<P, 1>(a, variant, grid, s);
+    if constexpr (Prec<P>::NB2 > 0)
+        if (spt == 2) return launch_step_shape<P, 2>(a, variant, grid, s);
+    return cudaErrorInvalidValue;
 }
 
 template <int P>
@@ -1165,7 +1356,7 @@ cudaError_t configure_prec() {
 }
 
 template cudaError_t configure_prec<LB_PREC>();
-template cudaError_t launch_step_prec<LB_PREC>(const void*, int, dim3, cudaStream_t);
+template cudaError_t launch_step_prec<LB_PREC>(const void*, int, int, dim3, cudaStream_t);
 template cudaError_t launch_observe_prec<LB_PREC>(const CUtensorMap*, const void*, dim3,
                                                   cudaStream_t);
 template <int P>

@@ -32,25 +32,26 @@ __device__ __forceinline__ C wgt(int i) {
 template <int P> struct Prec;
 // TX: tile width, chosen so that a deviation row with its 2-cell halo,
 // TX + 4, is a multiple of 32 (one cell per thread); NB: ring slots of
-// 8-row population blocks in the step kernel.  SCALE_LOG2: the stored value
-// is the offset times 2^SCALE_LOG2 (FP16: 2^10, which keeps offsets down to
-// 2^-24 in binary16's normal range, where rounding has its full 11 bits;
-// the largest storable offset becomes 64).
+// 8-row population blocks in the step kernel with 8-row tiles, NB2 with
+// 16-row tiles (0: no 16-row tile for this precision).  SCALE_LOG2: the
+// stored value is the offset times 2^SCALE_LOG2 (FP16: 2^10, which keeps
+// offsets down to 2^-24 in binary16's normal range, where rounding has its
+// full 11 bits; the largest storable offset becomes 64).
 template <> struct Prec<LB_FP64> {
     typedef double T; typedef double2 T2; typedef double C; typedef double2 C2;
-    static constexpr int GX = 4, TX = 28, TY = 8, NB = 3, SCALE_LOG2 = 0;
+    static constexpr int GX = 4, TX = 28, TY = 8, NB = 3, NB2 = 0, SCALE_LOG2 = 0;
 };
 template <> struct Prec<LB_FP32> {
     typedef float T; typedef float2 T2; typedef float C; typedef float2 C2;
-    static constexpr int GX = 4, TX = 60, TY = 8, NB = 4, SCALE_LOG2 = 0;
+    static constexpr int GX = 4, TX = 60, TY = 8, NB = 4, NB2 = 5, SCALE_LOG2 = 0;
 };
 template <> struct Prec<LB_FP16_OFFSET> {
     typedef __half T; typedef __half2 T2; typedef float C; typedef float2 C2;
-    static constexpr int GX = 8, TX = 60, TY = 8, NB = 4, SCALE_LOG2 = 10;
+    static constexpr int GX = 8, TX = 60, TY = 8, NB = 4, NB2 = 6, SCALE_LOG2 = 10;
 };
 template <> struct Prec<LB_BF16_OFFSET> {
     typedef __nv_bfloat16 T; typedef __nv_bfloat162 T2; typedef float C; typedef float2 C2;
-    static constexpr int GX = 8, TX = 60, TY = 8, NB = 4, SCALE_LOG2 = 0;
+    static constexpr int GX = 8, TX = 60, TY = 8, NB = 4, NB2 = 6, SCALE_LOG2 = 0;
 };
 // The storage scale of precision P and its inverse, in the compute type.
 template <int P> __host__ __device__ constexpr typename Prec<P>::C scale_of() {
@@ -195,22 +196,29 @@ __device__ __forceinline__ float2 pexpm1(float2 x) {
 __device__ __forceinline__ double csin(double v) { return sin(v); }
 __device__ __forceinline__ float csin(float v) { return sinf(v); }
 
-template <int P>
+// Shared-memory layout and thread mapping of the step kernel for precision P
+// and SPT sites per thread: SPT = 1, tiles of TX x 8 sites, one site per
+// thread, leaving through a staging tile and a TMA bulk store; SPT = 2,
+// tiles of TX x 16 sites, each thread updating two vertically adjacent
+// sites (sharing their stencil rows) and storing them to global memory
+// directly.  Both walk the same 8-row population blocks.
+template <int P, int SPT = 1>
 struct Layout {
     typedef typename Prec<P>::T T;
     typedef typename Prec<P>::T2 T2;
     typedef typename Prec<P>::C C;
     typedef typename Prec<P>::C2 C2;
-    static constexpr int TX = Prec<P>::TX, TY = Prec<P>::TY;
+    static constexpr int TX = Prec<P>::TX;
+    static constexpr int TYB = Prec<P>::TY;           // rows of a population block (8)
+    static constexpr int TY = TYB * SPT;              // tile rows
     static constexpr int GX = Prec<P>::GX;
     static constexpr int BX = TX + 2 * GX;            // box columns (sites)
-    static constexpr int BY = TY + 2 * kGY;           // observe box rows
-    static constexpr int RX = TX + 4, RY = TY + 4;    // rho/Psi tile (2-cell halo)
-    // threads: one per deviation cell of a tile's 8 new rows; in the site
-    // phase thread (lx, ly) = (tid % RX, tid / RX) updates site lx < TX
-    static constexpr int NT = RX * TY;
-    static constexpr int TYB = 8;                     // rows of a step-kernel block
-    static constexpr int NB = Prec<P>::NB;            // ring slots of blocks
+    static constexpr int BY = TYB + 2 * kGY;          // observe box rows
+    static constexpr int RX = TX + 4, RY = TYB + 4;   // rho/Psi tile (2-cell halo), observe
+    // threads: one per deviation column and block row; in the site phase
+    // thread (lx, j) = (tid % RX, tid / RX) updates sites (lx, SPT j + s), lx < TX
+    static constexpr int NT = RX * TYB;
+    static constexpr int NB = SPT == 1 ? Prec<P>::NB : Prec<P>::NB2;   // ring slots of blocks
     // rho/Psi deviation window of a tile: rows y0 - 2 .. y0 + TY + 1
     static constexpr int WIN = TY + 4;
     // step kernel: NB block slots, the rho and Psi windows, the staging tile
@@ -218,14 +226,15 @@ struct Layout {
     static constexpr int WIN_OFF = NB * SLOT_BYTES;
     static constexpr int WIN_BYTES = 2 * WIN * RX * (int)sizeof(C2);
     static constexpr int STAGE_OFF = WIN_OFF + WIN_BYTES;
-    static constexpr int STAGE_BYTES = 9 * TY * TX * (int)sizeof(T2);
+    static constexpr int STAGE_BYTES = SPT == 1 ? 9 * TY * TX * (int)sizeof(T2) : 0;
     static constexpr int SMEM = STAGE_OFF + STAGE_BYTES + 128;
     // observe kernel: one tile box and the rho/Psi tile
     static constexpr int BOX_BYTES = 9 * BY * BX * (int)sizeof(T2);
     static constexpr int BOX_STRIDE = (BOX_BYTES + 127) / 128 * 128;
     static constexpr int RHOPSI = (2 * RX * RY * (int)sizeof(C2) + 127) / 128 * 128;
     static constexpr int SMEM_OBS = BOX_STRIDE + RHOPSI + 128;
-    static_assert(TY == TYB, "a tile spans one block plus the halo of the next");
+    static_assert(SPT == 1 || SPT == 2, "one or two sites per thread");
+    static_assert(NB >= SPT + 2, "the ring holds a tile's blocks and at least one more");
     static_assert(RX % 32 == 0, "deviation rows are whole warps");
     static_assert((2 * TX * sizeof(T)) % 16 == 0 && (2 * (TX + GX) * sizeof(T)) % 16 == 0,
                   "TMA x coordinates of tiles stay 16-byte aligned");

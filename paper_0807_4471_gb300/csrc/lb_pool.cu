@@ -3,8 +3,8 @@
 //
 // Native runtime pieces: a first-fit arena allocator (one cudaMalloc at
 // creation), admission by footprint, the active-set bookkeeping, CUDA-graph
-// capture and replay of step chunks, and a measured autotuner of the work
-// partition cached per member-set signature.
+// capture and replay of step chunks, and a measured autotuner of the step
+// kernel's tile shape and work partition, cached per member-set signature.
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
@@ -23,7 +23,7 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int kGraphChunk = 16;   // steps per captured graph
-constexpr int kTuneSteps = 6;     // timed steps per candidate partition
+constexpr int kTuneSteps = 6;     // timed steps per candidate (tile shape, partition)
 // A new member set is tuned only if it runs at least kTuneShare times the
 // steps that timing all candidates takes: a short-lived set (a server's
 // quantum between arrivals) keeps the load-balance model's partition.
@@ -86,9 +86,16 @@ struct Member {
 
 }  // namespace
 
+// A launch configuration the tuner chooses: work partition and tile shape.
+struct Choice {
+    int seg;                 // > 0 segments of seg tiles; -1 contiguous runs; 0 the model's
+    int spt;                 // sites per thread (tiles of 8 spt rows)
+};
+
 struct lb_pool {
     lb_params shared;
     int forced_seg;          // 0: autotune; else the partition to use (-1: contiguous runs)
+    int forced_spt;          // 0: autotune; else the sites per thread to use
     cudaStream_t stream;
     bool own_stream;
     int device, sms;
@@ -107,7 +114,7 @@ struct lb_pool {
     bool built;
     Launch launch;
     cudaGraphExec_t graph;
-    std::map<std::string, int> tuned;   // member-set signature -> segment length
+    std::map<std::string, Choice> tuned;   // member-set signature -> tuned choice
 };
 
 namespace {
@@ -139,7 +146,7 @@ void drop_graph(lb_pool* P) {
     }
 }
 
-lb_status build(lb_pool* P, int seg) {
+lb_status build(lb_pool* P, Choice c) {
     drop_graph(P);
     std::vector<Lattice*> lats;
     for (int j : P->active) lats.push_back(&P->members[(size_t)j].lat);
@@ -163,7 +170,7 @@ lb_status build(lb_pool* P, int seg) {
     cudaError_t ce = kernels_configure(P->shared.precision);   // before any graph capture
     if (ce != cudaSuccess) return cuda_status(ce);
     lb_status s = launch_build(P->launch, lats.data(), nlat, P->desc_mem, P->slots, P->ticket,
-                               P->sms, P->stream, P->host_desc, seg);
+                               P->sms, P->stream, P->host_desc, c.seg, c.spt);
     P->built = s == LB_OK;
     return s;
 }
@@ -215,33 +222,61 @@ void advanced(lb_pool* P, long long k) {
     }
 }
 
-// Time kTuneSteps real steps for each candidate segment length and keep the
-// fastest.  Returns the steps consumed.
+// The choices open to the tuner (the fixed dimensions of lb_pool_set_partition
+// and lb_pool_set_tile_rows kept), and the untuned default.
+std::vector<Choice> candidates(lb_pool* P) {
+    const int prec = P->shared.precision;
+    std::vector<int> spts;
+    if (P->forced_spt != 0) spts.push_back(P->forced_spt);
+    else for (int k = 1; k <= max_spt(prec); ++k) spts.push_back(k);
+    std::vector<Choice> out;
+    for (int spt : spts) {
+        std::vector<int> segs;
+        if (P->forced_seg != 0) {
+            segs.push_back(P->forced_seg);
+        } else {
+            // contiguous runs per CTA, the load-balance model's segments, then fixed segments
+            std::vector<int> ns, nt;
+            int tiles = 0;
+            for (int j : P->active) {
+                const Lattice& L = P->members[(size_t)j].lat;
+                ns.push_back(L.nstrips);
+                nt.push_back(tiles_y(L, spt));
+                tiles = std::max(tiles, nt.back());
+            }
+            segs = {-1, choose_seg(ns.data(), nt.data(), (int)ns.size(), P->sms)};
+            for (int c : {1, 2, 4, 8, 16, 32, 64})
+                if (c <= tiles && std::find(segs.begin(), segs.end(), c) == segs.end()) segs.push_back(c);
+        }
+        for (int seg : segs) out.push_back({seg, spt});
+    }
+    return out;
+}
+Choice untuned(lb_pool* P) {
+    return {P->forced_seg, P->forced_spt != 0 ? P->forced_spt : default_spt(P->shared.precision)};
+}
+std::string cache_key(lb_pool* P) {
+    return signature(P) + "|" + std::to_string(P->forced_seg) + "|" + std::to_string(P->forced_spt);
+}
+
+// Time kTuneSteps real steps for each candidate (tile shape, partition) and
+// keep the fastest.  Returns the steps consumed.
 long long tune(lb_pool* P, long long budget_steps, lb_status* st) {
     *st = LB_OK;
-    std::vector<Lattice*> lats;
-    std::vector<int> ns, nt;
-    int tiles = 0;
-    for (int j : P->active) {
-        Lattice* L = &P->members[(size_t)j].lat;
-        lats.push_back(L);
-        ns.push_back(L->nstrips);
-        nt.push_back(L->ntiles_y);
-        tiles = std::max(tiles, L->ntiles_y);
+    const std::vector<Choice> cand = candidates(P);
+    if (cand.size() < 2) {   // nothing to choose between
+        *st = build(P, cand.empty() ? untuned(P) : cand[0]);
+        return 0;
     }
-    // contiguous runs per CTA, the load-balance model's segments, then fixed segments
-    std::vector<int> cand = {-1, choose_seg(ns.data(), nt.data(), (int)lats.size(), P->sms)};
-    for (int c : {1, 2, 4, 8, 16, 32, 64})
-        if (c <= tiles && std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
     if ((long long)cand.size() * kTuneSteps * kTuneShare > budget_steps) return 0;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    int best = cand[0];
+    Choice best = cand[0];
     float best_ms = 1e30f;
     long long used = 0;
-    for (int seg : cand) {
-        *st = build(P, seg);
+    for (const Choice& c : cand) {
+        *st = build(P, c);
         if (*st != LB_OK) break;
         cudaEventRecord(e0, P->stream);
         *st = run_steps(P, kTuneSteps);
@@ -254,13 +289,13 @@ long long tune(lb_pool* P, long long budget_steps, lb_status* st) {
         used += kTuneSteps;
         if (ms < best_ms) {
             best_ms = ms;
-            best = seg;
+            best = c;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (*st == LB_OK) {
-        P->tuned[signature(P)] = best;
+        P->tuned[cache_key(P)] = best;
         *st = build(P, best);
     }
     return used;
@@ -292,9 +327,8 @@ lb_status lb_pool_prepare(lb_pool* P) {
     if (act.empty()) return LB_OK;
     if (!P->built || act != P->active) {
         P->active = act;
-        auto it = P->tuned.find(signature(P));
-        const int seg = P->forced_seg != 0 ? P->forced_seg : (it != P->tuned.end() ? it->second : 0);
-        lb_status s = build(P, seg);
+        auto it = P->tuned.find(cache_key(P));
+        lb_status s = build(P, it != P->tuned.end() ? it->second : untuned(P));
         if (s != LB_OK) return s;
     }
     return capture_graph(P);
@@ -401,15 +435,13 @@ lb_status lb_pool_run(lb_pool* P, int64_t quantum, int32_t* active_out) {
         if (act.empty()) break;
         if (!P->built || act != P->active) {
             P->active = act;
-            auto it = P->tuned.find(signature(P));
-            if (P->forced_seg != 0) {
-                s = build(P, P->forced_seg);
-            } else if (it != P->tuned.end()) {
+            auto it = P->tuned.find(cache_key(P));
+            if (it != P->tuned.end()) {
                 s = build(P, it->second);
             } else {
                 const long long used = tune(P, k, &s);
                 if (s != LB_OK) return s;
-                if (used == 0) s = build(P, 0);   // too few steps to tune: the model's choice
+                if (!P->built) s = build(P, untuned(P));   // too few steps to tune
                 k -= used;
                 remaining -= used;
             }
@@ -485,7 +517,24 @@ lb_status lb_pool_set_partition(lb_pool* P, int32_t seg) {
     if (!P || seg < -1) return LB_ERR_INVALID;
     P->forced_seg = seg;
     P->built = false;   // rebuilt with it before the next step
+    drop_graph(P);
     return LB_OK;
+}
+
+lb_status lb_pool_set_tile_rows(lb_pool* P, int32_t rows) {
+    if (!P) return LB_ERR_INVALID;
+    const int ty = kernel_tile_y(P->shared.precision);
+    if (rows != 0 && rows != ty && rows != 2 * ty) return LB_ERR_INVALID;
+    const int spt = rows / ty;
+    if (spt > max_spt(P->shared.precision)) return LB_ERR_INVALID;
+    P->forced_spt = spt;
+    P->built = false;
+    drop_graph(P);
+    return LB_OK;
+}
+
+int32_t lb_pool_tile_rows(const lb_pool* P) {
+    return P && P->built ? P->launch.spt * kernel_tile_y(P->shared.precision) : 0;
 }
 
 lb_status lb_pool_destroy(lb_pool* P) {

@@ -34,20 +34,20 @@ def tile_cost(nx, ny, periodic, tx, sx, ty):
     return 1.26 if edge else 1.0
 
 
-def check_cover(items, cta, dims, tx, sms):
+def check_cover(items, cta, dims, tx, sms, ty_rows=TY):
     G = len(cta) - 1
     assert 1 <= G <= sms
     assert cta[0] == 0 and cta[-1] == len(items) and np.all(np.diff(cta) >= 1)
     seen = {}
     for l, sx, a, b in items:
         nx, ny, _ = dims[l]
-        nt = -(-ny // TY)
+        nt = -(-ny // ty_rows)
         assert 0 <= sx < -(-nx // tx) and 0 <= a < b <= nt
         for ty in range(a, b):
             key = (l, sx, ty)
             assert key not in seen, key
             seen[key] = True
-    want = sum(-(-nx // tx) * -(-ny // TY) for nx, ny, _ in dims)
+    want = sum(-(-nx // tx) * -(-ny // ty_rows) for nx, ny, _ in dims)
     assert len(seen) == want
 
 
@@ -149,3 +149,23 @@ def test_invalid_plans(lb):
         lb.lb_plan_partition(mixed, 0, 152)
     with pytest.raises(LbError):
         lb.lb_plan_partition(lattices(lb, [(64, 64, 0)]), 0, 0)
+
+
+@pytest.mark.parametrize("dims", CASES)
+@pytest.mark.parametrize("seg", [0, -1, 1, 3])
+def test_every_tile_once_16_row_tiles(lb, dims, seg):
+    """The two-sites-per-thread kernel's 16-row tiles: every tile once."""
+    items, cta, _ = lb.lb_plan_partition(lattices(lb, dims), seg, 152, tile_rows=16)
+    check_cover(items, cta, dims, TX["fp32"], 152, ty_rows=16)
+
+
+def test_tile_rows_validation(lb):
+    with pytest.raises(lb.LbError):
+        lb.lb_plan_partition(lattices(lb, [(64, 64, 0)]), 0, 152, tile_rows=12)
+    with pytest.raises(lb.LbError):        # FP64 has only the 8-row tile
+        lb.lb_plan_partition(lattices(lb, [(64, 64, 0)], "fp64"), 0, 152, tile_rows=16)
+    p = lb.make_params(64, 64, "fp64", tile_rows=16)
+    with pytest.raises(lb.LbError):
+        lb.lb_workspace_size(p)
+    for rows in (0, 8, 16):
+        assert lb.lb_workspace_size(lb.make_params(64, 64, "fp32", tile_rows=rows)) > 0
