@@ -435,6 +435,8 @@ lb_status lb_pool_run(lb_pool* P, int64_t quantum, int32_t* active_out) {
         if (act.empty()) break;
         if (!P->built || act != P->active) {
             P->active = act;
+            P->built = false;   // the previous member set's launch no longer applies
+            drop_graph(P);
             auto it = P->tuned.find(cache_key(P));
             if (it != P->tuned.end()) {
                 s = build(P, it->second);
