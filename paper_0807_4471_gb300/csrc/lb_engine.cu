@@ -435,11 +435,12 @@ void partition(Lattice* const* lats, int nlat, int seg, int spt, int sms, std::v
 }  // namespace
 
 // Default partition: cost-balanced contiguous runs while each CTA has up to
-// ~40 tiles (measured faster on 512^2-1024^2 lattices), the load-balance
-// model's dealt segments beyond (their CTAs sweep a band of rows together,
-// which keeps the halo columns in L2 on large lattices).
-static int default_seg(long long tiles, const int* ns, const int* nt, int nlat, int sms) {
-    return tiles <= 40LL * sms ? -1 : choose_seg(ns, nt, nlat, sms);
+// ~40 tiles of 8 rows (measured faster on 512^2-1024^2 lattices), the
+// load-balance model's dealt segments beyond (their CTAs sweep a band of
+// rows together, which keeps the halo columns in L2 on large lattices);
+// `tiles` counts tiles of 8 spt rows.
+static int default_seg(long long tiles, int spt, const int* ns, const int* nt, int nlat, int sms) {
+    return tiles * spt <= 40LL * sms ? -1 : choose_seg(ns, nt, nlat, sms);
 }
 
 // Host-only plan of a launch's work items (lb_plan_partition).
@@ -470,7 +471,7 @@ lb_status plan_partition(const lb_params* ps, int nlat, int seg, int tile_rows, 
         nt[(size_t)l] = tiles_y(L, spt);
         tiles += (long long)L.nstrips * nt[(size_t)l];
     }
-    const int s = seg != 0 ? seg : default_seg(tiles, ns.data(), nt.data(), nlat, sms);
+    const int s = seg != 0 ? seg : default_seg(tiles, spt, ns.data(), nt.data(), nlat, sms);
     std::vector<Item> it;
     std::vector<int> c;
     int G = 0;
@@ -507,7 +508,7 @@ lb_status launch_build(Launch& Ln, Lattice* const* lats, int nlat, void* descs, 
         tiles += (long long)lats[l]->nstrips * nt[(size_t)l];
         strips += lats[l]->nstrips;
     }
-    const int seg = forced_seg != 0 ? forced_seg : default_seg(tiles, ns.data(), nt.data(), nlat, sms);
+    const int seg = forced_seg != 0 ? forced_seg : default_seg(tiles, spt, ns.data(), nt.data(), nlat, sms);
     std::vector<Item> items;
     std::vector<int> cta;
     int grid = 0;

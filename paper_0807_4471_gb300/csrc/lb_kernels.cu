@@ -567,13 +567,13 @@ __device__ __forceinline__ void site_update(
 // to warps 2 and up: warps 0 and 1 have just issued the tile's loads and
 // store, and every warp waits for the last one at the next barrier.  Kept
 // out of the site update, whose register allocation it would otherwise
-// burden.
-template <int P, int NT>
+// burden.  L: the step kernel's layout (tile rows TY, staging layout).
+template <int P, class L>
 __device__ __forceinline__ void write_edges(const typename Prec<P>::T2* stage,
                                             typename Prec<P>::T2* fout, const Geom& g, int x0,
                                             int y0, bool per, int tid) {
     typedef typename Prec<P>::T2 T2;
-    constexpr int TX = Prec<P>::TX, TY = Prec<P>::TY;
+    constexpr int TX = L::TX, TY = L::TY, NT = L::NT;
     const int w = min(TX, g.nx - x0), h = min(TY, g.ny - y0);   // valid part of the tile
     // source columns [0, nca) and [cb0, w), rows [0, na) and [rb0, h); the
     // two ranges of each never meet since nx, ny >= 8
@@ -601,7 +601,7 @@ __device__ __forceinline__ void write_edges(const typename Prec<P>::T2* stage,
         }
         const int dX = lx < nca ? g.nx : (ncb > 0 && lx >= cb0 ? -g.nx : 0);
         const long long dY = ly < na ? SY : (nb > 0 && ly >= rb0 ? -SY : 0);
-        const T2 e = stage[(i * TY + ly) * TX + lx];
+        const T2 e = stage[L::stage_off(ly, lx) + i * L::TYB * TX];
         T2* d = fout + i * PL + (long long)(y0 + ly + kGY) * g.pitch + (x0 + lx + g.gx);
         if (dX) d[dX] = e;
         if (dY) {
@@ -645,13 +645,14 @@ __device__ __forceinline__ void block_sum4(double red[4], double (*s_red)[4]) {
 // and each deviation row computed once per strip, and only the x halo (4 of
 // 64 columns) is redundant.  Every thread keeps one column and SPT rows of
 // the window in both phases, so all its shared-memory addresses within a
-// slot are fixed.  SPT = 1: tiles leave through a staging tile by TMA bulk
-// tensor stores, clipped at the lattice edge, and tiles near an edge then
-// write the periodic ghost copies.  SPT = 2: each thread updates two
-// vertically adjacent sites, which share four of their six stencil rows,
-// and stores them (with their ghost copies) to global memory itself.  The
-// last CTA to finish advances every lattice's step counter and buffer
-// parity and takes the Couette wall samples.
+// slot are fixed.  SPT = 2: each thread updates two vertically adjacent
+// sites, which share four of their six stencil rows.  Tiles leave through a
+// staging tile by TMA bulk tensor stores (one per 8 rows), clipped at the
+// lattice edge, and tiles near an edge then write the periodic ghost
+// copies; where the staging tile does not fit beside the ring (FP32 with
+// 16-row tiles) the threads store their sites and ghost copies to global
+// memory themselves.  The last CTA to finish advances every lattice's step
+// counter and buffer parity and takes the Couette wall samples.
 // V: bit 0 = every lattice periodic (no wall code); bit 1 = general forcing.
 template <int P, int V, int SPT>
 __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
@@ -662,6 +663,7 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
     typedef typename L::C2 C2;
     constexpr bool ALLPER = (V & 1) != 0;
     constexpr bool GEN = (V & 2) != 0;
+    constexpr bool STAGED = L::STAGED;   // output through the staging tile
     constexpr int PS = L::TYB * L::BX;   // plane stride in a block slot (pairs)
     extern __shared__ unsigned char smem_raw[];
     // 128-byte aligned base, derived from the shared array by indexing so
@@ -669,7 +671,7 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
     unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     C2* win_r = reinterpret_cast<C2*>(smem + L::WIN_OFF);     // [WIN][RX]
     C2* win_p = win_r + L::WIN * L::RX;                       // [WIN][RX]
-    T2* stage = reinterpret_cast<T2*>(smem + L::STAGE_OFF);   // [9][TY][TX] (SPT = 1)
+    T2* stage = reinterpret_cast<T2*>(smem + L::STAGE_OFF);   // staging tile (STAGED)
     __shared__ __align__(8) uint64_t bars[L::NB];
     __shared__ int s_fail, s_last;
     __shared__ double s_red[L::NT / 32][4];
@@ -679,7 +681,7 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
     const int tid = threadIdx.x;
     const int G = gridDim.x;
     // thread 0 issues the block loads; this thread (warp 1) the bulk stores
-    // of the staging tile and the waits on them (SPT = 1)
+    // of the staging tile and the waits on them (STAGED)
     constexpr int kStoreThread = 32;
     // When one buffer of every lattice of the launch fits in L2 together, the
     // step's output stays there for the next step (evict last) and the input,
@@ -832,7 +834,7 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
                     win_p[k * L::RX + lx] = win_p[km * L::RX + lx];
                 }
             }
-            if (SPT == 1 && tid == kStoreThread) bulk_wait_read();   // previous bulk store has read the staging tile
+            if (STAGED && tid == kStoreThread) bulk_wait_read();   // previous bulk store has read the staging tile
             __syncthreads();
             if (s_fail) break;
 
@@ -840,29 +842,7 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
             // y0 + SPT t_j + s), whose stencil rows y - 2 .. y + 2 are window
             // rows SPT t_j + s .. SPT t_j + s + 4 and whose populations sit in
             // padded rows y0 + SPT t_j + s + 2 .. + 4.
-            if constexpr (SPT == 1) {
-                const int lx = t_lx, ly = t_j;
-                const int x = x0 + lx, y = y0 + ly;
-                if (lx < L::TX && x < g.nx && y < g.ny) {
-                    const int bc = lx + L::GX;
-                    C2 fx[1], fy[1], qx[1], qy[1], dp[1], dr[1];
-                    force_sums<1, L::RX>(win_p + ly * L::RX + lx + 2, win_r + ly * L::RX + lx + 2,
-                                         a.k, fx, fy, qx, qy, dp, dr);
-                    SiteOut<T2> o;
-                    o.stage = stage + ly * L::TX + lx;
-                    o.key = key;
-                    o.obs = OBS_NONE;
-                    double wr[4] = {0.0, 0.0, 0.0, 0.0};
-                    site_update<P, false, GEN, PS, SINK_STAGE>(
-                        brow(ly + 2, bc), brow(ly + 3, bc), brow(ly + 4, bc), fx[0], fy[0], qx[0],
-                        qy[0], dp[0], dr[0], x, y, per, pull, g, v, a.k, o, wr, bad);
-                    if (!per && (y == 0 || y == g.ny - 1)) {   // FP64: wall rows only
-                        wall[0] += wr[0];
-                        wall[1] += wr[1];
-                    }
-                    fence_proxy_async();   // staging writes before the bulk store
-                }
-            } else {
+            {
                 const int lx = t_lx, ly = SPT * t_j;
                 const int x = x0 + lx, y = y0 + ly;
                 if (lx < L::TX && x < g.nx && y < g.ny) {
@@ -871,21 +851,27 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
                     force_sums<SPT, L::RX>(win_p + ly * L::RX + lx + 2,
                                            win_r + ly * L::RX + lx + 2, a.k, fx, fy, qx, qy, dp, dr);
                     SiteOut<T2> o;
-                    o.plane = g.plane;
-                    o.gdx = x < 3 ? g.nx : (x >= g.nx - 3 ? -g.nx : 0);
-                    o.pol = s_pol[1];
                     o.key = key;
                     o.obs = OBS_NONE;
+                    if constexpr (!STAGED) {
+                        o.plane = g.plane;
+                        o.gdx = x < 3 ? g.nx : (x >= g.nx - 3 ? -g.nx : 0);
+                        o.pol = s_pol[1];
+                    }
 #pragma unroll
                     for (int s = 0; s < SPT; ++s) {
                         const int ys = y + s;
                         if (s > 0 && ys >= g.ny) break;
-                        o.gout = fout + (long long)(ys + kGY) * g.pitch + (x + g.gx);
-                        o.gdy = !per ? 0
-                                : ys < 3 ? (long long)g.ny * g.pitch
-                                : (ys >= g.ny - 3 ? -(long long)g.ny * g.pitch : 0);
+                        if constexpr (STAGED) {
+                            o.stage = stage + L::stage_off(ly + s, lx);
+                        } else {
+                            o.gout = fout + (long long)(ys + kGY) * g.pitch + (x + g.gx);
+                            o.gdy = !per ? 0
+                                    : ys < 3 ? (long long)g.ny * g.pitch
+                                    : (ys >= g.ny - 3 ? -(long long)g.ny * g.pitch : 0);
+                        }
                         double wr[4] = {0.0, 0.0, 0.0, 0.0};
-                        site_update<P, false, GEN, PS, SINK_GLOBAL>(
+                        site_update<P, false, GEN, PS, STAGED ? SINK_STAGE : SINK_GLOBAL>(
                             brow(ly + s + 2, bc), brow(ly + s + 3, bc), brow(ly + s + 4, bc), fx[s],
                             fy[s], qx[s], qy[s], dp[s], dr[s], x, ys, per, pull, g, v, a.k, o, wr,
                             bad);
@@ -894,17 +880,22 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
                             wall[1] += wr[1];
                         }
                     }
+                    if constexpr (STAGED) fence_proxy_async();   // staging writes before the bulk store
                 }
             }
             __syncthreads();
-            if constexpr (SPT == 1) {
-                // The bulk store and the next loads are issued by two threads
+            if constexpr (STAGED) {
+                // The bulk stores and the next loads are issued by two threads
                 // of different warps, side by side.
                 if (tid == kStoreThread) {
-                    // site (x0, y0) in padded coordinates: pair column x0 + gx,
-                    // row y0 + kGY; a ragged tile's store is clipped at x = nx, y = ny
-                    tma_store_3d_hint(&d->tout[cur ^ 1], stage, 2 * (x0 + L::GX), y0 + kGY, 0,
-                                      s_pol[1]);
+                    // site (x0, y0 + 8h) in padded coordinates: pair column
+                    // x0 + gx, row y0 + 8h + kGY; a ragged tile's store is
+                    // clipped at x = nx, y = ny (no box starts below the lattice)
+#pragma unroll
+                    for (int h = 0; h < SPT; ++h)
+                        if (h == 0 || y0 + h * L::TYB < g.ny)
+                            tma_store_3d_hint(&d->tout[cur ^ 1], stage + L::stage_off(h * L::TYB, 0),
+                                              2 * (x0 + L::GX), y0 + h * L::TYB + kGY, 0, s_pol[1]);
                     bulk_commit();
                 }
             }
@@ -914,11 +905,11 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
                 fence_proxy_async();   // generic reads of freed slots before async writes
                 while (p_pos < released + L::NB && issue_next()) {}
             }
-            if constexpr (SPT == 1) {
+            if constexpr (STAGED) {
                 // only tiles within 3 sites of an edge write periodic ghost copies
                 const bool edge = x0 < 3 || x0 + L::TX > g.nx - 3 ||
                                   (per && (y0 < 3 || y0 + L::TY > g.ny - 3));
-                if (edge) write_edges<P, L::NT>(stage, fout, g, x0, y0, per, tid);
+                if (edge) write_edges<P, L>(stage, fout, g, x0, y0, per, tid);
             }
         }
         if (bad) {   // a density of this lattice went non-finite
@@ -957,7 +948,7 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
             }
         }
     }
-    if (SPT == 1 && tid == kStoreThread) bulk_wait_all();
+    if (STAGED && tid == kStoreThread) bulk_wait_all();
     if (s_fail && tid == 0) {
         // Let copies in flight land before the CTA exits.  No slot is
         // re-armed once a wait has failed, so the last NB positions issued

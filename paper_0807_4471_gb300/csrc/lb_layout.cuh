@@ -221,19 +221,30 @@ struct Layout {
     static constexpr int NB = SPT == 1 ? Prec<P>::NB : Prec<P>::NB2;   // ring slots of blocks
     // rho/Psi deviation window of a tile: rows y0 - 2 .. y0 + TY + 1
     static constexpr int WIN = TY + 4;
-    // step kernel: NB block slots, the rho and Psi windows, the staging tile
+    // step kernel: NB block slots, the rho and Psi windows, and -- where it
+    // fits -- the staging tile of the bulk tensor stores, [TY / 8][9][8][TX]
+    // (8-row halves, each one box of the 8-row store descriptor); without it
+    // (FP32 with 16-row tiles) the threads store to global memory directly
     static constexpr int SLOT_BYTES = 9 * TYB * BX * (int)sizeof(T2);
     static constexpr int WIN_OFF = NB * SLOT_BYTES;
     static constexpr int WIN_BYTES = 2 * WIN * RX * (int)sizeof(C2);
     static constexpr int STAGE_OFF = WIN_OFF + WIN_BYTES;
-    static constexpr int STAGE_BYTES = SPT == 1 ? 9 * TY * TX * (int)sizeof(T2) : 0;
+    static constexpr int STAGE_FULL = 9 * TY * TX * (int)sizeof(T2);
+    static constexpr bool STAGED = STAGE_OFF + STAGE_FULL + 128 <= 227 * 1024 - 1024;
+    static constexpr int STAGE_BYTES = STAGED ? STAGE_FULL : 0;
     static constexpr int SMEM = STAGE_OFF + STAGE_BYTES + 128;
+    // staging slot (plane 0) of tile row ly, column lx: planes of a half are
+    // 8 TX pairs apart
+    static __host__ __device__ constexpr int stage_off(int ly, int lx) {
+        return ((ly >> 3) * 9) * TYB * TX + (ly & (TYB - 1)) * TX + lx;
+    }
     // observe kernel: one tile box and the rho/Psi tile
     static constexpr int BOX_BYTES = 9 * BY * BX * (int)sizeof(T2);
     static constexpr int BOX_STRIDE = (BOX_BYTES + 127) / 128 * 128;
     static constexpr int RHOPSI = (2 * RX * RY * (int)sizeof(C2) + 127) / 128 * 128;
     static constexpr int SMEM_OBS = BOX_STRIDE + RHOPSI + 128;
     static_assert(SPT == 1 || SPT == 2, "one or two sites per thread");
+    static_assert(SPT == 1 || STAGED || sizeof(T2) == 8, "direct stores: FP32 pairs only");
     static_assert(NB >= SPT + 2, "the ring holds a tile's blocks and at least one more");
     static_assert(RX % 32 == 0, "deviation rows are whole warps");
     static_assert((2 * TX * sizeof(T)) % 16 == 0 && (2 * (TX + GX) * sizeof(T)) % 16 == 0,
