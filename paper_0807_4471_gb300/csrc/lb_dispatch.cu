@@ -20,6 +20,7 @@ int kernel_ghost_x(int p) { LB_SWITCH(p, return Layout<P>::GX) return 0; }
 int kernel_elem_bytes(int p) { LB_SWITCH(p, return (int)sizeof(typename Layout<P>::T)) return 0; }
 int kernel_smem_obs_bytes(int p) { LB_SWITCH(p, return Layout<P>::SMEM_OBS) return 0; }
 int kernel_block_rows(int p) { LB_SWITCH(p, return Layout<P>::TYB) return 0; }
+int kernel_scale_log2(int p) { LB_SWITCH(p, return Prec<P>::SCALE_LOG2) return 0; }
 
 cudaError_t launch_step(int precision, const void* args, int variant, int spt, dim3 grid,
                         cudaStream_t s) {

@@ -149,10 +149,20 @@ static void fill_coef(Coef<C>& k, const lb_params* p) {
     k.psi_ref = (C)(pref * (1.0 - std::exp(-rref / p->rho0)));
     k.psi_scale = (C)(pref * std::exp(-rref / p->rho0));
     k.inv_rho0 = (C)(1.0 / p->rho0);
-    k.tau[0] = (C)p->tau_A;
-    k.tau[1] = (C)p->tau_B;
+    k.tau3[0] = (C)(3.0 * p->tau_A);
+    k.tau3[1] = (C)(3.0 * p->tau_B);
     k.omega[0] = (C)(1.0 / p->tau_A);
     k.omega[1] = (C)(1.0 / p->tau_B);
+    // omega w times the storage scale (a power of two: exact), per class of
+    // |c_i|^2; the products are rounded once, in the compute precision
+    const double sc = std::ldexp(1.0, kernel_scale_log2(p->precision));
+    const double wc[3] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 36.0};
+    for (int c = 0; c < 3; ++c) {
+        k.omw[c].x = (C)(sc * wc[c] / p->tau_A);
+        k.omw[c].y = (C)(sc * wc[c] / p->tau_B);
+    }
+    k.omm.x = (C)(1.0 - 1.0 / p->tau_A);
+    k.omm.y = (C)(1.0 - 1.0 / p->tau_B);
     k.u_wall = (C)p->u_wall;
     k.g_x = (C)p->g_x;
     k.kolmo_amp = (C)p->kolmo_amp;

@@ -71,8 +71,10 @@ struct Coef {
     C psi_scale;       // P exp(-rho_ref / rho0)
     C inv_rho0;        // 1 / rho0
     C rho_ref;         // reference density of the stored offsets
-    C tau[2];          // relaxation times
+    C tau3[2];         // 3 tau_s (the velocity shift is taken for v = 3u)
     C omega[2];        // 1 / tau
+    C2 omw[3];         // omega_s S w for the D2Q9 classes |c|^2 = 0, 1, 2 (S the storage scale)
+    C2 omm;            // 1 - omega_s
     C u_wall;          // Couette wall speed (top +, bottom -)
     C g_x;             // uniform body acceleration
     C kolmo_amp;       // Kolmogorov acceleration amplitude
@@ -152,6 +154,7 @@ int kernel_ghost_x(int precision);
 int kernel_elem_bytes(int precision);
 int kernel_smem_obs_bytes(int precision);
 int kernel_block_rows(int precision);
+int kernel_scale_log2(int precision);
 
 // Step: the persistent multi-lattice kernel (args: BatchArgs<C>), variant
 // bit 0 = every lattice periodic, bit 1 = general forcing, spt sites per

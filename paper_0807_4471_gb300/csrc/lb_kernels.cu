@@ -234,30 +234,32 @@ __device__ __forceinline__ void cell_dev(const typename Prec<P>::T2* bm,
 }
 
 // Post-collision offsets of both species (Eq. (1), BGK toward the
-// equilibrium at velocity (ux, uy), per species):
-// h*_i = h_i + omega (heq_i - h_i) [+ 3 w_i c_i . F for the source scheme],
-// heq_i = f^eq_i - w_i rho_ref = w_i [d_rho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u^2)],
-// evaluated per pair (i, opp(i)), whose c.u differ only in sign:
-// heq = E +- O with E = w (d_rho - 1.5 rho u^2 + 4.5 rho (c.u)^2), O = 3 w rho c.u.
-// h and out are in the storage scale SC (a power of two), folded into w.
+// equilibrium at velocity u, per species), written with v = 3u:
+//   h*_i = (1 - omega) h_i + omega heq_i [+ 3 w_i c_i . F for the source scheme],
+//   heq_i = f^eq_i - w_i rho_ref = w_i [d_rho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u^2)]
+//         = w_i [Q + rho (c.v) + rho (c.v)^2 / 2],  Q = d_rho - rho v^2 / 6,
+// evaluated per pair (i, opp(i)), whose c.v differ only in sign:
+// heq = w (g +- rho c.v) with g = Q + rho (c.v)^2 / 2.  h and out are in
+// the storage scale SC (a power of two); k.omw holds omega SC w per class
+// of |c|^2 and k.omm = 1 - omega.
 template <typename C, typename C2, bool SRC>
-__device__ __forceinline__ void collide(const C2 h[9], C2 out[9], C2 drho, C2 rho, C2 ux, C2 uy,
-                                        C2 om, C2 Fx, C2 Fy, C SC) {
-    const C2 Q = pfma(pmul(rho, pset(C(-1.5))), pfma(ux, ux, pmul(uy, uy)), drho);
-    out[0] = pfma(om, psub(pmul(pset(SC * wgt<C>(0)), Q), h[0]), h[0]);
+__device__ __forceinline__ void collide(const C2 h[9], C2 out[9], C2 drho, C2 rho, C2 vx, C2 vy,
+                                        const Coef<C>& k, C2 Fx, C2 Fy, C SC) {
+    const C2 Q = pfma(pmul(rho, pset(C(-1) / C(6))), pfma(vx, vx, pmul(vy, vy)), drho);
+    out[0] = pfma(k.omw[0], Q, pmul(k.omm, h[0]));
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int i = k == 0 ? 1 : (k == 1 ? 2 : (k == 2 ? 5 : 6));   // c.u = ux, uy, ux+uy, uy-ux
+    for (int q = 0; q < 4; ++q) {
+        const int i = q == 0 ? 1 : (q == 1 ? 2 : (q == 2 ? 5 : 6));   // c.v = vx, vy, vx+vy, vy-vx
         const int j = opp(i);
-        const C2 cu = k == 0 ? ux : (k == 1 ? uy : (k == 2 ? padd(ux, uy) : psub(uy, ux)));
-        const C w = SC * wgt<C>(i);
-        const C2 rcu = pmul(rho, cu);
-        const C2 E = pmul(pset(w), pfma(pmul(pset(C(4.5)), cu), rcu, Q));
-        const C2 O = pmul(pset(C(3) * w), rcu);
-        out[i] = pfma(om, psub(padd(E, O), h[i]), h[i]);
-        out[j] = pfma(om, psub(psub(E, O), h[j]), h[j]);
+        const C2 cv = q == 0 ? vx : (q == 1 ? vy : (q == 2 ? padd(vx, vy) : psub(vy, vx)));
+        const C2 ow = k.omw[q < 2 ? 1 : 2];
+        const C2 rv = pmul(rho, cv);
+        const C2 g = pfma(rv, pmul(cv, pset(C(0.5))), Q);
+        out[i] = pfma(ow, padd(g, rv), pmul(k.omm, h[i]));
+        out[j] = pfma(ow, psub(g, rv), pmul(k.omm, h[j]));
         if (SRC) {
-            const C2 S = pmul(pset(C(3) * w), pfma(pset(C(cx(i))), Fx, pmul(pset(C(cy(i))), Fy)));
+            const C w3 = C(3) * SC * wgt<C>(i);
+            const C2 S = pmul(pset(w3), pfma(pset(C(cx(i))), Fx, pmul(pset(C(cy(i))), Fy)));
             out[i] = padd(out[i], S);
             out[j] = psub(out[j], S);
         }
@@ -473,26 +475,27 @@ __device__ __forceinline__ void site_update(
     }
 
     // Eq. (1): forced BGK relaxation.  Common velocity
-    // u' = sum_s (j_s/tau_s) / sum_s (rho_s/tau_s); shift u_s = u' + tau_s F_s/rho_s.
-    // (selects, not branches: an empty site has u' = 0 and no shift)
+    // u' = sum_s (j_s/tau_s) / sum_s (rho_s/tau_s); shift u_s = u' + tau_s F_s/rho_s;
+    // carried as v = 3u.  (Selects, not branches: an empty site has u' = 0
+    // and no shift.)
     const C2 om = pair(k.omega[0], k.omega[1]);
     const C2 ro = pmul(rho, om), jxo = pmul(jx, om), jyo = pmul(jy, om);
     const C den = ro.x + ro.y;
-    const C inv = den != C(0) ? recip(den) : C(0);
-    const C2 up = pair((jxo.x + jxo.y) * inv, (jyo.x + jyo.y) * inv);
+    const C inv3 = den != C(0) ? C(3) * recip(den) : C(0);
+    const C2 vp = pair((jxo.x + jxo.y) * inv3, (jyo.x + jyo.y) * inv3);
     const bool source = GEN && k.source;
-    C2 ux = pset(up.x), uy = pset(up.y);
+    C2 vx = pset(vp.x), vy = pset(vp.y);
     if (!source) {
-        const C2 tr = pair(rho.x != C(0) ? k.tau[0] * recip(rho.x) : C(0),
-                           rho.y != C(0) ? k.tau[1] * recip(rho.y) : C(0));
-        ux = pfma(tr, Fx, ux);
-        uy = pfma(tr, Fy, uy);
+        const C2 tr = pair(rho.x != C(0) ? k.tau3[0] * recip(rho.x) : C(0),
+                           rho.y != C(0) ? k.tau3[1] * recip(rho.y) : C(0));
+        vx = pfma(tr, Fx, vx);
+        vy = pfma(tr, Fy, vy);
     }
     C2 hs[9];
     if (source)
-        collide<C, C2, true>(h, hs, drho, rho, ux, uy, om, Fx, Fy, scale_of<P>());
+        collide<C, C2, true>(h, hs, drho, rho, vx, vy, k, Fx, Fy, scale_of<P>());
     else
-        collide<C, C2, false>(h, hs, drho, rho, ux, uy, om, Fx, Fy, scale_of<P>());
+        collide<C, C2, false>(h, hs, drho, rho, vx, vy, k, Fx, Fy, scale_of<P>());
     T2 e[9];
     if constexpr (sizeof(T2) == 4) {
         if (k.sr) {   // half formats: random bits from (site, step), one word per pair
@@ -762,19 +765,32 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
         const uint32_t key = hash32((uint32_t)*((volatile long long*)&d->st->t) * 0x9e3779b9u);
         T2* fout = reinterpret_cast<T2*>(d->fbuf[cur ^ 1]);
         double wall[2] = {0.0, 0.0};
+        // ring slot and phase parity of the tile's first block, kept as the
+        // tiles advance
+        int qm = c_pos % L::NB, qph = (c_pos / L::NB) & 1;
         for (int ty = ty_a; ty < ty_b; ++ty) {
             const int q = c_pos + SPT * (ty - ty_a);   // this tile uses blocks q .. q + SPT
-            // each thread sees the blocks land itself; a timeout is acted on
-            // after the next barrier (garbage read meanwhile is harmless)
+            // Each thread sees the blocks land itself (the first block of a
+            // tile after an item's first was seen as the previous tile's
+            // last); a timeout is acted on after the next barrier (garbage
+            // read meanwhile is harmless).
+            int sl[SPT + 1];
 #pragma unroll
-            for (int b = 0; b <= SPT; ++b)
-                if (!mbar_wait_bounded(&bars[(q + b) % L::NB], ((q + b) / L::NB) & 1)) s_fail = 1;
+            for (int b = 0; b <= SPT; ++b) {
+                int sb = qm + b, ph = qph;
+                if (sb >= L::NB) {
+                    sb -= L::NB;
+                    ph ^= 1;
+                }
+                sl[b] = sb;
+                if ((b > 0 || ty == ty_a) && !mbar_wait_bounded(&bars[sb], ph)) s_fail = 1;
+            }
             const int y0 = ty * L::TY;
             // The tile's padded rows [y0, y0 + 8 (SPT + 1)) are blocks q ..
             // q + SPT; brow(r, c): padded row y0 + r, pair column c, plane 0.
-            const T2* s0 = slot(q);
-            const T2* s1 = slot(q + 1);
-            const T2* s2 = SPT > 1 ? slot(q + 2) : s1;
+            const T2* s0 = reinterpret_cast<const T2*>(smem + sl[0] * L::SLOT_BYTES);
+            const T2* s1 = reinterpret_cast<const T2*>(smem + sl[1] * L::SLOT_BYTES);
+            const T2* s2 = reinterpret_cast<const T2*>(smem + sl[SPT] * L::SLOT_BYTES);
             auto brow = [&](int r, int c) {
                 const T2* base = r < L::TYB ? s0 : (SPT == 1 || r < 2 * L::TYB ? s1 : s2);
                 return base + (r & (L::TYB - 1)) * L::BX + c;
@@ -910,6 +926,11 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
                 const bool edge = x0 < 3 || x0 + L::TX > g.nx - 3 ||
                                   (per && (y0 < 3 || y0 + L::TY > g.ny - 3));
                 if (edge) write_edges<P, L>(stage, fout, g, x0, y0, per, tid);
+            }
+            qm += SPT;
+            if (qm >= L::NB) {
+                qm -= L::NB;
+                qph ^= 1;
             }
         }
         if (bad) {   // a density of this lattice went non-finite
