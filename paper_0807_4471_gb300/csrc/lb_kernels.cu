@@ -400,6 +400,9 @@ struct SiteOut {
     int gdx;               // SINK_GLOBAL: offset of the periodic image in x (0: none)
     uint64_t pol;          // SINK_GLOBAL: L2 policy of the stores
     uint32_t key;          // stochastic rounding: hash of the lattice's step
+    int valid;             // 0: a site beyond the lattice, computed only to keep
+                           // the site updates of a thread free of branches:
+                           // its global stores and non-finite flag are dropped
     int obs;               // ObsKind (observe kernel) or OBS_NONE
     double* obs_out;
     int q0, q1;
@@ -431,7 +434,7 @@ __device__ __forceinline__ void site_update(
         jx = pmul(jx, pset(inv_scale_of<P>()));
         jy = pmul(jy, pset(inv_scale_of<P>()));
     }
-    if (!(isfinite(rho.x) && isfinite(rho.y))) bad = true;
+    if (o.valid && !(isfinite(rho.x) && isfinite(rho.y))) bad = true;
 
     // Eq. (2): F_s = -Psi_s(r) sum_d K_s(d) d Psi_s(r + d)
     //               - (G_X/rho0) rho_s(r) sum_d w(d) d rho_s'(r + d);
@@ -522,9 +525,11 @@ __device__ __forceinline__ void site_update(
         // Straight to the output buffer, and to the periodic images of a
         // site within three sites of an edge (ghost columns, and ghost rows
         // when periodic in y).
+        if (o.valid) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) st_pair(o.gout + i * o.plane, e[i], o.pol);
-        if (o.gdx != 0 || o.gdy != 0) {
+            for (int i = 0; i < 9; ++i) st_pair(o.gout + i * o.plane, e[i], o.pol);
+        }
+        if (o.valid && (o.gdx != 0 || o.gdy != 0)) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 T2* d = o.gout + i * o.plane;
@@ -805,33 +810,38 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
             // cells in this phase.
             {
                 const int bc = t_lx - 2 + L::GX;   // pair column in the block
+                // rows 0 .. 3: carried forward, or computed at an item's first
+                // tile, before this thread's new rows overwrite their sources
 #pragma unroll
                 for (int c = 0; c < SPT; ++c) {
                     const int k = 4 + SPT * t_j + c;
                     const int kk = k - L::TY;
                     if (kk >= 0) {
                         if (ty == ty_a) {
-                            const int y = y0 - 2 + kk;
-                            if (per || (y >= 0 && y < g.ny)) {
-                                C2 r, p;
-                                cell_dev<P, PS>(brow(kk, bc), brow(kk + 1, bc), brow(kk + 2, bc), y,
-                                                per, pull, g, v, r, p);
-                                win_r[kk * L::RX + t_lx] = r;
-                                win_p[kk * L::RX + t_lx] = p;
-                            }
+                            C2 r, p;
+                            cell_dev<P, PS>(brow(kk, bc), brow(kk + 1, bc), brow(kk + 2, bc),
+                                            y0 - 2 + kk, per, pull, g, v, r, p);
+                            win_r[kk * L::RX + t_lx] = r;
+                            win_p[kk * L::RX + t_lx] = p;
                         } else {
                             win_r[kk * L::RX + t_lx] = win_r[k * L::RX + t_lx];
                             win_p[kk * L::RX + t_lx] = win_p[k * L::RX + t_lx];
                         }
                     }
-                    const int y = y0 - 2 + k;
-                    if (per || y < g.ny) {
-                        C2 r, p;
-                        cell_dev<P, PS>(brow(k, bc), brow(k + 1, bc), brow(k + 2, bc), y, per, pull,
-                                        g, v, r, p);
-                        win_r[k * L::RX + t_lx] = r;
-                        win_p[k * L::RX + t_lx] = p;
-                    }
+                }
+                // The new rows, without a branch between the cells.  Rows
+                // outside the lattice (beyond a wall, or below a ragged last
+                // tile) are computed from whatever the slots hold there (the
+                // TMA fill or ghost rows): no site reads them -- the wall
+                // mirror below overwrites the two rows past each wall.
+#pragma unroll
+                for (int c = 0; c < SPT; ++c) {
+                    const int k = 4 + SPT * t_j + c;
+                    C2 r, p;
+                    cell_dev<P, PS>(brow(k, bc), brow(k + 1, bc), brow(k + 2, bc), y0 - 2 + k, per,
+                                    pull, g, v, r, p);
+                    win_r[k * L::RX + t_lx] = r;
+                    win_p[k * L::RX + t_lx] = p;
                 }
             }
             // mirror the deviations about the halfway walls, in the tiles whose
@@ -869,15 +879,19 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
                     SiteOut<T2> o;
                     o.key = key;
                     o.obs = OBS_NONE;
+                    o.valid = 1;
                     if constexpr (!STAGED) {
                         o.plane = g.plane;
                         o.gdx = x < 3 ? g.nx : (x >= g.nx - 3 ? -g.nx : 0);
                         o.pol = s_pol[1];
                     }
+                    // Both sites are updated without a branch between them (a
+                    // site below the lattice's last row, in a ragged tile, is
+                    // computed and dropped), so their work can interleave.
 #pragma unroll
                     for (int s = 0; s < SPT; ++s) {
                         const int ys = y + s;
-                        if (s > 0 && ys >= g.ny) break;
+                        o.valid = s == 0 || ys < g.ny;
                         if constexpr (STAGED) {
                             o.stage = stage + L::stage_off(ly + s, lx);
                         } else {
@@ -1099,6 +1113,7 @@ __global__ void __launch_bounds__(Layout<P>::NT)
             SiteOut<T2> o;
             o.stage = nullptr;
             o.key = 0u;
+            o.valid = 1;
             o.obs = a.obs;
             o.obs_out = a.obs_out;
             o.q0 = a.q0;
