@@ -347,6 +347,8 @@ def main():
                     help="untimed seconds of steps before the warm-up (clock record under load)")
     ap.add_argument("--batch-steps", type=int, default=lbinputs.CFG_BATCH_STEPS,
                     help="steps of every lattice of the 64-lattice batch")
+    ap.add_argument("--boundary", default="periodic", choices=["periodic", "couette"],
+                    help="the sweep lattices' boundary (couette: moving walls, shear rate 1e-4)")
     ap.add_argument("--tile-rows", type=int, default=0,
                     help="fix the step kernel's tile height (8 or 16; 0: autotuned with the partition)")
     ap.add_argument("--serve-jobs", type=int, default=2000)
@@ -379,15 +381,17 @@ def main():
     nx, ny, prec = args.nx, args.ny, args.precision
     rho0s = list(cfg["rho0s"][:args.lattices])
     stream = torch.cuda.Stream()
+    wall = {} if args.boundary == "periodic" else dict(
+        boundary=lb.LB_COUETTE, u_wall=lbinputs.wall_speed(1e-4, ny), init_shear=1)
     shared = lb.make_params(nx, ny, prec, psi_form=lb.LB_PSI_RHO0)
-    budget = sum(lb.Pool.footprint(lb.make_params(nx, ny, prec, rho0=r0, psi_form=lb.LB_PSI_RHO0))
-                 for r0 in rho0s) + (64 << 20)
+    budget = sum(lb.Pool.footprint(lb.make_params(nx, ny, prec, rho0=r0, psi_form=lb.LB_PSI_RHO0,
+                                                  **wall)) for r0 in rho0s) + (64 << 20)
     pool = lb.Pool(shared, budget, max_jobs=len(rho0s), stream=stream)
     if args.tile_rows:
         pool.set_tile_rows(args.tile_rows)
     # members run until released: the untimed set-up, warm-up, timed and
     # end-to-end steps all come out of one long schedule
-    jobs = [pool.admit(lb.make_params(nx, ny, prec, rho0=r0, psi_form=lb.LB_PSI_RHO0),
+    jobs = [pool.admit(lb.make_params(nx, ny, prec, rho0=r0, psi_form=lb.LB_PSI_RHO0, **wall),
                        cfg["seed"], 1 << 40) for r0 in rho0s]
 
     def barrier():
@@ -521,7 +525,7 @@ def main():
             "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f16-offset storage, f32 math",
                       "bf16": "bf16-offset storage, f32 math"}[prec],
             "data": "synthetic",
-            "config": {"workload": f"rho0 sweep, {len(rho0s)} x {nx}x{ny} periodic lattices, "
+            "config": {"workload": f"rho0 sweep, {len(rho0s)} x {nx}x{ny} {args.boundary} lattices, "
                                    f"{prec} storage; a bench step is one LB step of all of them, "
                                    "one persistent launch (lattice pool, CUDA-graph replay)",
                        "nx": nx, "ny": ny, "lattices": len(rho0s),

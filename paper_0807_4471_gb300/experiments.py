@@ -13,6 +13,8 @@
   interface of circular drops, p_in - p_out = sigma / R (Fig. 2, left).
 * couette_study: time-averaged wall stress and effective viscosity of plane
   Couette runs over shear rates and storage precisions.
+* sweep_structure_factor: the rho0 sweep at 512^2 with S(k) and the domain
+  length every 10^4 steps, for comparing storage precisions statistically.
 
 The host code here only samples fields (lb_fields) and reduces them with
 numpy; every time step runs in the library's kernels.
@@ -257,6 +259,38 @@ def couette_ensemble(lb, rate: float, seeds, precision: str = "fp32", n: int = 2
         return [float(pool.stress(j)["sigma_mean"]) for j in jobs]
 
 
+def sweep_structure_factor(lb, rho0s=(0.55, 0.65, 0.70, 0.75, 0.83), precision: str = "fp32",
+                           n: int = 512, steps: int = 100_000, every: int = 10_000, seed: int = 1,
+                           psi_form: int = 1, **kw):
+    """The rho0 sweep at the paper's resolution: one periodic n x n lattice
+    per rho0 (seeded, all stepped together in one pool), the radially binned
+    structure factor S(k) of phi = rho_A - rho_B and its domain length every
+    `every` steps.  Returns {"k": ring centres, "t": sample times,
+    "rho0": {rho0: {"S": [S(k) per sample], "L": [domain length per sample]}}}."""
+    ps = [lb.make_params(n, n, precision, rho0=r0, psi_form=psi_form, **kw) for r0 in rho0s]
+    budget = sum(lb.Pool.footprint(p) for p in ps) + (64 << 20)
+    out = {"t": [], "rho0": {float(r0): {"S": [], "L": []} for r0 in rho0s}}
+    with lb.Pool(ps[0], budget, max_jobs=len(ps)) as pool:
+        jobs = [pool.admit(p, seed, steps) for p in ps]
+        t = 0
+        while True:
+            if t > 0:
+                out["t"].append(t)
+                for r0, j in zip(rho0s, jobs):
+                    ra, rb, _, _ = pool.fields(j)
+                    k, S, _ = structure_factor(ra - rb)
+                    rec = out["rho0"][float(r0)]
+                    rec["S"].append(S.tolist())
+                    rec["L"].append(domain_length(ra - rb))
+                    out["k"] = k.tolist()
+            if t >= steps:
+                break
+            step = min(every, steps - t)
+            pool.run(step)
+            t += step
+    return out
+
+
 def ensemble_statistics(lb, precision: str, seeds, n: int = 128, steps: int = 2000, **kw):
     """Per-seed domain length and phi variance after `steps` steps of seeded
     periodic lattices stepped together in one pool."""
@@ -285,6 +319,7 @@ def main(argv=None):
         python -m paper_0807_4471_gb300.experiments couette --precisions fp64,fp32,fp16,bf16
         python -m paper_0807_4471_gb300.experiments couette-ensemble --rate 1e-4
         python -m paper_0807_4471_gb300.experiments statistics --steps 2000
+        python -m paper_0807_4471_gb300.experiments sweep --precisions fp64,fp32,fp16,bf16
     """
     import argparse
     import json
@@ -293,7 +328,7 @@ def main(argv=None):
 
     ap = argparse.ArgumentParser(prog="python -m paper_0807_4471_gb300.experiments")
     ap.add_argument("study", choices=["kolmogorov", "ageing", "laplace", "couette",
-                                      "couette-ensemble", "statistics"])
+                                      "couette-ensemble", "statistics", "sweep"])
     ap.add_argument("--psi-form", type=int, default=1)
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--precisions", default="fp64,fp32,fp16,bf16")
@@ -331,6 +366,10 @@ def main(argv=None):
         rates = [float(v) for v in np.logspace(-6, -4, 8)]
         res = couette_study(lb, rates, precisions=tuple(precs), n=a.n or 512,
                             steps=a.steps or 200_000, avg_from=(a.steps or 200_000) // 2, **kw)
+    elif a.study == "sweep":
+        res = {p: sweep_structure_factor(lb, precision=p, n=a.n or 512, steps=a.steps or 100_000,
+                                         every=a.every if a.every != 20_000 else 10_000, **kw)
+               for p in precs}
     elif a.study == "couette-ensemble":
         res = {p: couette_ensemble(lb, a.rate, range(a.seeds), precision=p, n=a.n or 256,
                                    steps=a.steps or 100_000, **kw) for p in precs}

@@ -118,3 +118,21 @@ def test_laplace_driver_on_oracle(O, caption):
     assert out["uniform"] and out["sigma"] > 0
     assert r1["dp"] > r2["dp"] > 0
     assert abs(r1["dp"] * r1["R"] / (r2["dp"] * r2["R"]) - 1) < 0.2
+
+
+def test_sweep_driver_on_oracle(O, caption):
+    """The rho0-sweep driver on oracle lattices: one S(k) and domain length
+    per lattice and sample time, S(k) summing to the variance of phi."""
+    lb = _OracleLb(O, caption)
+    out = E.sweep_structure_factor(lb, rho0s=(0.55, 0.83), precision="fp64", n=24, steps=60,
+                                   every=30, seed=1)
+    assert out["t"] == [30, 60] and set(out["rho0"]) == {0.55, 0.83}
+    for rec in out["rho0"].values():
+        assert len(rec["S"]) == 2 and len(rec["L"]) == 2
+        assert all(np.isfinite(rec["L"])) and all(v > 0 for v in rec["L"])
+    P = lb.make_params(24, 24, rho0=0.83, psi_form=1).P
+    f = O.init_seeded(P, 1)
+    O.run(P, f, 60)
+    ra, rb, _, _ = O.fields(P, f)
+    k, S, c = E.structure_factor(ra - rb)
+    assert np.allclose(out["rho0"][0.83]["S"][1], S, rtol=1e-12, atol=0)
