@@ -27,6 +27,7 @@
 
 #include <cstdint>
 #include <cstdlib>
+#include <type_traits>
 
 #include "lb_internal.h"
 #include "lb_layout.cuh"
@@ -763,7 +764,7 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
         const int ty_b = w.w;
         const Geom g = d->g;
         const LatVals<C> v = d->v;
-        const bool per = ALLPER || g.periodic;
+        const bool per_lat = ALLPER || g.periodic;
         const int cur = *((volatile int*)&d->st->cur);
         const int pull = *((volatile int*)&d->st->pull);
         // the step counter advances only after every CTA of the launch is done
@@ -801,118 +802,136 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
                 return base + (r & (L::TYB - 1)) * L::BX + c;
             };
 
-            // Phase 2: window row k holds lattice row y0 - 2 + k (padded row
-            // y0 + 1 + k).  Rows 4 .. TY + 3 are new: thread row t_j computes
-            // rows 4 + SPT t_j + c, c < SPT.  Rows 0 .. 3 are the previous
-            // tile's rows TY .. TY + 3, carried forward by the threads that
-            // own those before they overwrite them, or at an item's first
-            // tile computed from block q.  No other thread touches these
-            // cells in this phase.
-            {
-                const int bc = t_lx - 2 + L::GX;   // pair column in the block
-                // rows 0 .. 3: carried forward, or computed at an item's first
-                // tile, before this thread's new rows overwrite their sources
-#pragma unroll
-                for (int c = 0; c < SPT; ++c) {
-                    const int k = 4 + SPT * t_j + c;
-                    const int kk = k - L::TY;
-                    if (kk >= 0) {
-                        if (ty == ty_a) {
-                            C2 r, p;
-                            cell_dev<P, PS>(brow(kk, bc), brow(kk + 1, bc), brow(kk + 2, bc),
-                                            y0 - 2 + kk, per, pull, g, v, r, p);
-                            win_r[kk * L::RX + t_lx] = r;
-                            win_p[kk * L::RX + t_lx] = p;
-                        } else {
-                            win_r[kk * L::RX + t_lx] = win_r[k * L::RX + t_lx];
-                            win_p[kk * L::RX + t_lx] = win_p[k * L::RX + t_lx];
+            // The tile's two phases, with or without the wall code: a tile
+            // whose deviation window (rows y0 - 2 .. y0 + TY + 1) keeps clear
+            // of the walls and of the periodic ghost rows runs the periodic
+            // code, which is exact there, so only the tiles at a wall pay for
+            // the wall logic.  Returns false when a block wait gave up.
+            auto tile_body = [&](auto wall_tag) -> bool {
+                constexpr bool W = decltype(wall_tag)::value;
+                const bool per = !W || per_lat;
+                // Phase 2: window row k holds lattice row y0 - 2 + k (padded row
+                // y0 + 1 + k).  Rows 4 .. TY + 3 are new: thread row t_j computes
+                // rows 4 + SPT t_j + c, c < SPT.  Rows 0 .. 3 are the previous
+                // tile's rows TY .. TY + 3, carried forward by the threads that
+                // own those before they overwrite them, or at an item's first
+                // tile computed from block q.  No other thread touches these
+                // cells in this phase.
+                {
+                    const int bc = t_lx - 2 + L::GX;   // pair column in the block
+                    // rows 0 .. 3: carried forward, or computed at an item's first
+                    // tile, before this thread's new rows overwrite their sources
+    #pragma unroll
+                    for (int c = 0; c < SPT; ++c) {
+                        const int k = 4 + SPT * t_j + c;
+                        const int kk = k - L::TY;
+                        if (kk >= 0) {
+                            if (ty == ty_a) {
+                                C2 r, p;
+                                cell_dev<P, PS>(brow(kk, bc), brow(kk + 1, bc), brow(kk + 2, bc),
+                                                y0 - 2 + kk, per, pull, g, v, r, p);
+                                win_r[kk * L::RX + t_lx] = r;
+                                win_p[kk * L::RX + t_lx] = p;
+                            } else {
+                                win_r[kk * L::RX + t_lx] = win_r[k * L::RX + t_lx];
+                                win_p[kk * L::RX + t_lx] = win_p[k * L::RX + t_lx];
+                            }
                         }
                     }
+                    // The new rows, without a branch between the cells.  Rows
+                    // outside the lattice (beyond a wall, or below a ragged last
+                    // tile) are computed from whatever the slots hold there (the
+                    // TMA fill or ghost rows): no site reads them -- the wall
+                    // mirror below overwrites the two rows past each wall.
+    #pragma unroll
+                    for (int c = 0; c < SPT; ++c) {
+                        const int k = 4 + SPT * t_j + c;
+                        C2 r, p;
+                        cell_dev<P, PS>(brow(k, bc), brow(k + 1, bc), brow(k + 2, bc), y0 - 2 + k, per,
+                                        pull, g, v, r, p);
+                        win_r[k * L::RX + t_lx] = r;
+                        win_p[k * L::RX + t_lx] = p;
+                    }
                 }
-                // The new rows, without a branch between the cells.  Rows
-                // outside the lattice (beyond a wall, or below a ragged last
-                // tile) are computed from whatever the slots hold there (the
-                // TMA fill or ghost rows): no site reads them -- the wall
-                // mirror below overwrites the two rows past each wall.
-#pragma unroll
-                for (int c = 0; c < SPT; ++c) {
-                    const int k = 4 + SPT * t_j + c;
-                    C2 r, p;
-                    cell_dev<P, PS>(brow(k, bc), brow(k + 1, bc), brow(k + 2, bc), y0 - 2 + k, per,
-                                    pull, g, v, r, p);
-                    win_r[k * L::RX + t_lx] = r;
-                    win_p[k * L::RX + t_lx] = p;
+                // mirror the deviations about the halfway walls, in the tiles whose
+                // window rows y0 - 2 .. y0 + TY + 1 reach past a wall (uniform)
+                if (!per && (y0 < 2 || y0 + L::TY + 1 >= g.ny)) {
+                    __syncthreads();
+                    for (int c = tid; c < L::WIN * L::RX; c += L::NT) {
+                        const int k = c / L::RX, lx = c - k * L::RX;
+                        const int y = y0 - 2 + k;
+                        int ym;
+                        if (y < 0) ym = -1 - y;
+                        else if (y >= g.ny && y <= g.ny + 1) ym = 2 * g.ny - 1 - y;
+                        else continue;
+                        const int km = ym - (y0 - 2);   // in [0, WIN): see the wall cases
+                        win_r[k * L::RX + lx] = win_r[km * L::RX + lx];
+                        win_p[k * L::RX + lx] = win_p[km * L::RX + lx];
+                    }
                 }
-            }
-            // mirror the deviations about the halfway walls, in the tiles whose
-            // window rows y0 - 2 .. y0 + TY + 1 reach past a wall (uniform)
-            if (!per && (y0 < 2 || y0 + L::TY + 1 >= g.ny)) {
+                if (STAGED && tid == kStoreThread) bulk_wait_read();   // previous bulk store has read the staging tile
                 __syncthreads();
-                for (int c = tid; c < L::WIN * L::RX; c += L::NT) {
-                    const int k = c / L::RX, lx = c - k * L::RX;
-                    const int y = y0 - 2 + k;
-                    int ym;
-                    if (y < 0) ym = -1 - y;
-                    else if (y >= g.ny && y <= g.ny + 1) ym = 2 * g.ny - 1 - y;
-                    else continue;
-                    const int km = ym - (y0 - 2);   // in [0, WIN): see the wall cases
-                    win_r[k * L::RX + lx] = win_r[km * L::RX + lx];
-                    win_p[k * L::RX + lx] = win_p[km * L::RX + lx];
-                }
-            }
-            if (STAGED && tid == kStoreThread) bulk_wait_read();   // previous bulk store has read the staging tile
-            __syncthreads();
-            if (s_fail) break;
+                if (s_fail) return false;
 
-            // Phase 3: SPT sites per thread (lx < TX): sites (x0 + t_lx,
-            // y0 + SPT t_j + s), whose stencil rows y - 2 .. y + 2 are window
-            // rows SPT t_j + s .. SPT t_j + s + 4 and whose populations sit in
-            // padded rows y0 + SPT t_j + s + 2 .. + 4.
-            {
-                const int lx = t_lx, ly = SPT * t_j;
-                const int x = x0 + lx, y = y0 + ly;
-                if (lx < L::TX && x < g.nx && y < g.ny) {
-                    const int bc = lx + L::GX;
-                    C2 fx[SPT], fy[SPT], qx[SPT], qy[SPT], dp[SPT], dr[SPT];
-                    force_sums<SPT, L::RX>(win_p + ly * L::RX + lx + 2,
-                                           win_r + ly * L::RX + lx + 2, a.k, fx, fy, qx, qy, dp, dr);
-                    SiteOut<T2> o;
-                    o.key = key;
-                    o.obs = OBS_NONE;
-                    o.valid = 1;
-                    if constexpr (!STAGED) {
-                        o.plane = g.plane;
-                        o.gdx = x < 3 ? g.nx : (x >= g.nx - 3 ? -g.nx : 0);
-                        o.pol = s_pol[1];
-                    }
-                    // Both sites are updated without a branch between them (a
-                    // site below the lattice's last row, in a ragged tile, is
-                    // computed and dropped), so their work can interleave.
-#pragma unroll
-                    for (int s = 0; s < SPT; ++s) {
-                        const int ys = y + s;
-                        o.valid = s == 0 || ys < g.ny;
-                        if constexpr (STAGED) {
-                            o.stage = stage + L::stage_off(ly + s, lx);
-                        } else {
-                            o.gout = fout + (long long)(ys + kGY) * g.pitch + (x + g.gx);
-                            o.gdy = !per ? 0
-                                    : ys < 3 ? (long long)g.ny * g.pitch
-                                    : (ys >= g.ny - 3 ? -(long long)g.ny * g.pitch : 0);
+                // Phase 3: SPT sites per thread (lx < TX): sites (x0 + t_lx,
+                // y0 + SPT t_j + s), whose stencil rows y - 2 .. y + 2 are window
+                // rows SPT t_j + s .. SPT t_j + s + 4 and whose populations sit in
+                // padded rows y0 + SPT t_j + s + 2 .. + 4.
+                {
+                    const int lx = t_lx, ly = SPT * t_j;
+                    const int x = x0 + lx, y = y0 + ly;
+                    if (lx < L::TX && x < g.nx && y < g.ny) {
+                        const int bc = lx + L::GX;
+                        C2 fx[SPT], fy[SPT], qx[SPT], qy[SPT], dp[SPT], dr[SPT];
+                        force_sums<SPT, L::RX>(win_p + ly * L::RX + lx + 2,
+                                               win_r + ly * L::RX + lx + 2, a.k, fx, fy, qx, qy, dp, dr);
+                        SiteOut<T2> o;
+                        o.key = key;
+                        o.obs = OBS_NONE;
+                        o.valid = 1;
+                        if constexpr (!STAGED) {
+                            o.plane = g.plane;
+                            o.gdx = x < 3 ? g.nx : (x >= g.nx - 3 ? -g.nx : 0);
+                            o.pol = s_pol[1];
                         }
-                        double wr[4] = {0.0, 0.0, 0.0, 0.0};
-                        site_update<P, false, GEN, PS, STAGED ? SINK_STAGE : SINK_GLOBAL>(
-                            brow(ly + s + 2, bc), brow(ly + s + 3, bc), brow(ly + s + 4, bc), fx[s],
-                            fy[s], qx[s], qy[s], dp[s], dr[s], x, ys, per, pull, g, v, a.k, o, wr,
-                            bad);
-                        if (!per && (ys == 0 || ys == g.ny - 1)) {   // FP64: wall rows only
-                            wall[0] += wr[0];
-                            wall[1] += wr[1];
+                        // Both sites are updated without a branch between them (a
+                        // site below the lattice's last row, in a ragged tile, is
+                        // computed and dropped), so their work can interleave.
+    #pragma unroll
+                        for (int s = 0; s < SPT; ++s) {
+                            const int ys = y + s;
+                            o.valid = s == 0 || ys < g.ny;
+                            if constexpr (STAGED) {
+                                o.stage = stage + L::stage_off(ly + s, lx);
+                            } else {
+                                o.gout = fout + (long long)(ys + kGY) * g.pitch + (x + g.gx);
+                                o.gdy = !per ? 0
+                                        : ys < 3 ? (long long)g.ny * g.pitch
+                                        : (ys >= g.ny - 3 ? -(long long)g.ny * g.pitch : 0);
+                            }
+                            double wr[4] = {0.0, 0.0, 0.0, 0.0};
+                            site_update<P, false, GEN, PS, STAGED ? SINK_STAGE : SINK_GLOBAL>(
+                                brow(ly + s + 2, bc), brow(ly + s + 3, bc), brow(ly + s + 4, bc), fx[s],
+                                fy[s], qx[s], qy[s], dp[s], dr[s], x, ys, per, pull, g, v, a.k, o, wr,
+                                bad);
+                            if (!per && (ys == 0 || ys == g.ny - 1)) {   // FP64: wall rows only
+                                wall[0] += wr[0];
+                                wall[1] += wr[1];
+                            }
                         }
+                        if constexpr (STAGED) fence_proxy_async();   // staging writes before the bulk store
                     }
-                    if constexpr (STAGED) fence_proxy_async();   // staging writes before the bulk store
                 }
-            }
+                return true;
+            };
+            bool ok;
+            if constexpr (ALLPER)
+                ok = tile_body(std::false_type{});
+            else if (per_lat || (y0 >= 3 && y0 + L::TY + 3 <= g.ny))
+                ok = tile_body(std::false_type{});
+            else
+                ok = tile_body(std::true_type{});
+            if (!ok) break;
             __syncthreads();
             if constexpr (STAGED) {
                 // The bulk stores and the next loads are issued by two threads
@@ -938,8 +957,8 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
             if constexpr (STAGED) {
                 // only tiles within 3 sites of an edge write periodic ghost copies
                 const bool edge = x0 < 3 || x0 + L::TX > g.nx - 3 ||
-                                  (per && (y0 < 3 || y0 + L::TY > g.ny - 3));
-                if (edge) write_edges<P, L>(stage, fout, g, x0, y0, per, tid);
+                                  (per_lat && (y0 < 3 || y0 + L::TY > g.ny - 3));
+                if (edge) write_edges<P, L>(stage, fout, g, x0, y0, per_lat, tid);
             }
             qm += SPT;
             if (qm >= L::NB) {
@@ -953,7 +972,7 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
         }
         if (s_fail) break;
         c_pos += SPT * (ty_b - ty_a) + 1;
-        if (!per && (ty_a == 0 || ty_b == d->ntiles_y)) {
+        if (!per_lat && (ty_a == 0 || ty_b == d->ntiles_y)) {
             // Wall momentum of an item holding a wall row (only these items'
             // slots are read), in FP64.  FP64 issues at a small fraction of
             // the FP32 rate, so only the warps that updated a wall site
