@@ -93,6 +93,9 @@ static Geom make_geom(const lb_params* p) {
     g.plane = (long long)g.rows * g.pitch;
     g.gx = gx;
     g.periodic = p->boundary == LB_PERIODIC ? 1 : 0;
+    // the tile stores end at the last 16-byte boundary of a row's lattice part
+    const int pair_bytes = 2 * es;
+    g.x_tail = (p->nx + gx) * pair_bytes / 16 * 16 / pair_bytes - gx;
     return g;
 }
 
@@ -255,10 +258,13 @@ lb_status lattice_setup(Lattice& L, const lb_params* p, char* region) {
     lb_status s = LB_OK;
     for (int b = 0; b < 2 && s == LB_OK; ++b) {
         s = make_tmap(&L.tblock[b], p->precision, L.g, L.fbuf[b], bx, kernel_block_rows(p->precision));
-        // tile stores end at the lattice's last column and row: the ghost
-        // columns and rows beyond a ragged tile are never written by them
+        // Tile stores end at the lattice's last row and at the last 16-byte
+        // boundary of its rows (x_tail): a clipped bulk store writes up to a
+        // 16-byte boundary, which would reach into the ghost column beside
+        // an unaligned last lattice column and race with the plain stores
+        // of the ghost copies.  Columns x_tail .. nx - 1 get plain stores.
         if (s == LB_OK)
-            s = make_tmap(&L.ttile[b], p->precision, L.g, L.fbuf[b], tx, ty, p->nx + L.g.gx,
+            s = make_tmap(&L.ttile[b], p->precision, L.g, L.fbuf[b], tx, ty, L.g.x_tail + L.g.gx,
                           p->ny + kGY);
         if (s == LB_OK) s = make_tmap(&L.tobs[b], p->precision, L.g, L.fbuf[b], bx, ty + 2 * kGY);
     }

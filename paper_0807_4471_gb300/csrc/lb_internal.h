@@ -48,6 +48,11 @@ struct Geom {
     long long plane;    // pairs per direction plane = rows * pitch
     int gx;             // ghost columns on each side
     int periodic;       // 1: periodic in y; 0: Couette walls in y
+    // Lattice columns x >= x_tail (at most 3) are written by plain stores,
+    // not by the tile's bulk tensor store: a clipped bulk store ends on a
+    // 16-byte boundary, so its descriptor stops at the last 16-byte
+    // boundary of the lattice row and leaves the ghost column beside it alone.
+    int x_tail;
 };
 
 // The (A, B) pair type of a compute precision.

@@ -570,7 +570,9 @@ __device__ __forceinline__ void site_update(
 
 // Periodic images of one tile's edge sites, from the staging tile into the
 // ghost columns (x within 3 of either edge) and, when the lattice is
-// periodic in y, the ghost rows (y within 3 of either edge) and corners; by
+// periodic in y, the ghost rows (y within 3 of either edge) and corners, and
+// the sites themselves in the last lattice columns the bulk store leaves
+// out (x >= x_tail, within 3 of the right edge); by
 // all NT threads of the CTA, one (site, plane) copy each in turn, with
 // consecutive threads on consecutive sites of a plane.  The first copies go
 // to warps 2 and up: warps 0 and 1 have just issued the tile's loads and
@@ -612,6 +614,7 @@ __device__ __forceinline__ void write_edges(const typename Prec<P>::T2* stage,
         const long long dY = ly < na ? SY : (nb > 0 && ly >= rb0 ? -SY : 0);
         const T2 e = stage[L::stage_off(ly, lx) + i * L::TYB * TX];
         T2* d = fout + i * PL + (long long)(y0 + ly + kGY) * g.pitch + (x0 + lx + g.gx);
+        if (x0 + lx >= g.x_tail) d[0] = e;
         if (dX) d[dX] = e;
         if (dY) {
             d[dY] = e;

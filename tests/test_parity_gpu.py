@@ -7,7 +7,10 @@ max |rho|), on the plain-method configuration (Psi prefactor rho0).  The
 paper's sqrt(rho0) prefactor drives a faster demixing instability: there a
 half-ulp FP64 perturbation per step already grows to 6e-12 in 100 steps, so
 that form is held to the same tolerances at 50 steps.  Lattices span several
-tiles and ragged tails (the FP64 tile is 28 x 8 sites, the FP32/half tile 60 x 8).
+tiles and ragged tails (the FP64 tile is 28 x 8 sites, the FP32/half tiles
+60 x 8 and 60 x 16), including widths whose last lattice column does not end
+a 16-byte unit of the row (33, 61, 131 in FP32; 130, 33 in the half formats),
+where the tile's bulk store stops short and plain stores finish the row.
 """
 import numpy as np
 import pytest
@@ -177,7 +180,8 @@ def test_fp32_plain_config(lb, O, psi_form, steps):
     g.close()
 
 
-@pytest.mark.parametrize("nx,ny,boundary", [(72, 40, 0), (100, 27, 1), (8, 8, 0)])
+@pytest.mark.parametrize("nx,ny,boundary", [(72, 40, 0), (100, 27, 1), (8, 8, 0), (33, 17, 1),
+                                             (61, 13, 0), (131, 21, 1)])
 def test_fp32_ragged(lb, O, nx, ny, boundary):
     m = model(nx, ny, boundary=boundary, u_wall=0.03 if boundary else 0.0)
     P, f, _, g = run_both(lb, O, m, 20, precision="fp32", seed=4)
@@ -229,7 +233,8 @@ def test_nonfinite_is_reported(lb):
 @pytest.mark.parametrize("fmt", ["fp16", "bf16"])
 @pytest.mark.parametrize("boundary", [0, 1])
 @pytest.mark.parametrize("rounding", [0, 1])
-def test_half_offset_one_step(lb, O, fmt, boundary, rounding):
+@pytest.mark.parametrize("dims", [(72, 40), (130, 9), (33, 17)])
+def test_half_offset_one_step(lb, O, fmt, boundary, rounding, dims):
     """One step from the same quantised state: the oracle advances the
     quantised initial populations in FP64 and the result is compared, as
     offsets h = f - w_i rho_ref, with the GPU's 16-bit output (FP32
@@ -240,7 +245,7 @@ def test_half_offset_one_step(lb, O, fmt, boundary, rounding):
     unbiased) within five standard deviations."""
     from _pair import offsets, round_bf16, round_half, ulp16
     rnd = round_half if fmt == "fp16" else round_bf16
-    m = model(72, 40, boundary=boundary, u_wall=0.02 if boundary else 0.0)
+    m = model(*dims, boundary=boundary, u_wall=0.02 if boundary else 0.0)
     P = oracle_params(O, m)
     rref = float(np.float32(m["rho0"]))       # offsets are taken from rho_ref in FP32
     p = gpu_params(lb, m, fmt)
@@ -271,7 +276,7 @@ def test_half_offset_one_step(lb, O, fmt, boundary, rounding):
             inner &= np.abs(want) >= 2.0 ** -24
         n_up, expect = up[inner].sum(), frac[inner].sum()
         sd = np.sqrt((frac[inner] * (1 - frac[inner])).sum())
-        assert inner.sum() > 1000
+        assert inner.sum() > 200
         assert abs(n_up - expect) < 5 * sd, (n_up, expect, sd)
     g.close()
 

@@ -40,7 +40,7 @@ def run_single(lb, m, prec, rows, seed, steps, fields=False):
 
 
 DIMS = [(72, 40, 0), (100, 27, 1), (8, 8, 0), (60, 16, 1), (130, 9, 0), (1020, 136, 1),
-        (512, 512, 0)]
+        (512, 512, 0), (33, 17, 1), (131, 21, 0)]
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
