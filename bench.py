@@ -356,7 +356,12 @@ def main():
                     help="factor on the served jobs' step counts")
     ap.add_argument("--lattices", type=int, default=len(lbinputs.CFG_SWEEP["rho0s"]),
                     help="number of sweep lattices stepped per bench step (profiling runs)")
+    ap.add_argument("--kernel-hash", action="store_true",
+                    help="print the step kernel's source hash (as the traffic record keys it) and exit")
     args = ap.parse_args()
+    if args.kernel_hash:
+        print(kernel_hash())
+        return 0
     if args.steps is None:
         args.steps = 200 if args.impl == "reference" else 5000
     args.warmup = max(args.warmup, 3)
