@@ -494,7 +494,15 @@ def main():
                 mlups, gbs = peak_lattice(torch, lb, p, lbinputs.CFG_PEAK["nx"], 50, rows)
                 by_rows[rows] = {"MLUPS": mlups, "GB_per_s_alg": gbs, "frac_hbm": gbs / hbm_peak}
             best = max(by_rows, key=lambda r: by_rows[r]["MLUPS"])
-            extra[f"peak_{p}_4096"] = dict(by_rows[best], tile_rows=best,
+            n = lbinputs.CFG_PEAK["nx"]
+            gbs = by_rows[best]["GB_per_s_alg"]
+            # the HBM-roofline claim of the step kernel: inputs far larger than L2
+            roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": gbs / hbm_peak, "peak_kind": peak_kind,
+                    "bytes_per_launch_alg": BYTES_PER_SITE[p] * n * n,
+                    "traffic": ncu_traffic("k_step", p, f"1x{n}x{n}") if best == 16 else None,
+                    "traffic_source": "profiles/traffic.json (ncu, 16-row tiles, this kernel source)"}
+            extra[f"peak_{p}_4096"] = dict(by_rows[best], tile_rows=best, roofline=roof,
                                            by_tile_rows={str(r): v for r, v in by_rows.items()})
         extra["batched_64_fp16"] = batched_mix(torch, lb, args.batch_steps)
         extra["batched_64_fp32"] = batched_mix(torch, lb, args.batch_steps, "fp32")
