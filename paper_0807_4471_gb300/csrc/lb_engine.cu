@@ -327,6 +327,7 @@ static void fill_desc(LatDesc<C>& d, const Lattice& L, const Coef<C>& k, int wal
     d.ntiles_y = ntiles;
     d.stress_every = L.p.stress_every;
     d.stress_t0 = L.p.stress_t0;
+    d.inv_nx = 1.0 / L.p.nx;
 }
 
 size_t launch_area_doubles(size_t tiles, size_t strips, int sms) {
@@ -356,9 +357,10 @@ void partition(Lattice* const* lats, int nlat, int seg, int spt, int sms, std::v
         tiles += (long long)lats[l]->nstrips * nty[(size_t)l];
     }
     // Tile costs measured on GB300, relative to a full interior tile: tiles
-    // that write periodic ghost copies 1.26, ragged tiles 1.04, and the first
-    // tile of an item one tile more (its block ring fills and it computes 12
-    // deviation rows).
+    // that write periodic ghost copies, and Couette tiles holding a wall row
+    // (mirror, bounce-back, wall momentum), 1.26; ragged tiles 1.04; and the
+    // first tile of an item one tile more (its block ring fills and it
+    // computes four more deviation rows).
     auto cost = [&](int l, int sx, int ty) {
         const Lattice& L = *lats[l];
         const int tx = kernel_tile_x(L.p.precision), tyy = kernel_tile_y(L.p.precision) * spt;
@@ -366,7 +368,8 @@ void partition(Lattice* const* lats, int nlat, int seg, int spt, int sms, std::v
         const bool full = x0 + tx <= L.p.nx && y0 + tyy <= L.p.ny;
         if (!full) return 1.04;
         const bool per = L.g.periodic != 0;
-        const bool edge = x0 < 3 || x0 + tx > L.p.nx - 3 || (per && (y0 < 3 || y0 + tyy > L.p.ny - 3));
+        const bool edge = x0 < 3 || x0 + tx > L.p.nx - 3 || (per && (y0 < 3 || y0 + tyy > L.p.ny - 3)) ||
+                          (!per && (y0 == 0 || y0 + tyy >= L.p.ny));
         return edge ? 1.26 : 1.0;
     };
     const double kItemStart = 1.0;

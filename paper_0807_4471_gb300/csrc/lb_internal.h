@@ -102,7 +102,7 @@ struct LatVals {
 template <typename C>
 struct alignas(128) LatDesc {
     CUtensorMap tin[2];    // 8-row block loads of buffer b: box {2 BX, 8, 9}
-    CUtensorMap tout[2];   // tile stores into buffer b: box {2 TX, TY, 9}, clipped at x = nx, y = ny
+    CUtensorMap tout[2];   // tile stores into buffer b: box {2 TX, 8, 9}, clipped at x = x_tail, y = ny
     Geom g;
     LatVals<C> v;
     void* fbuf[2];
@@ -112,6 +112,7 @@ struct alignas(128) LatDesc {
     int ntiles_y;          // tile rows of the launch's tile shape
     int stress_every;
     long long stress_t0;
+    double inv_nx;         // 1 / nx: the wall samples are momentum per unit length
 };
 
 // Arguments of the (multi-lattice) step kernel.

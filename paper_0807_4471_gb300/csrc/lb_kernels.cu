@@ -544,27 +544,23 @@ __device__ __forceinline__ void site_update(
     }
     if (!per && (y == 0 || y == g.ny - 1)) {
         // x-momentum handed to the wall by the links that will bounce back
-        // at the next streaming: c_x (f*_i + f_opp), f_opp = f*_i - 6 w_i
-        // rho_w (c_i . u_w), from the stored (rounded) values.
+        // at the next streaming, from the stored (rounded) values:
+        // sum_i c_ix (f*_i + f_opp), f_opp = f*_i - 6 w_i rho_w (c_i . u_w),
+        // over the three links i leaving through the wall, which is
+        // 2 (f*_a - f*_b) - 6 rho_w u_w (w_a + w_b) = 2 (f*_a - f*_b) - rho_w u_w / 3
+        // with (a, b) = (8, 7) at the bottom wall and (5, 6) at the top
+        // (c_ax = 1, c_bx = -1; w_a = w_b, so the offsets' difference is the
+        // populations').  One FP32 value per site and species, one FP64 add.
         const int down = (y == 0);
         const C uw = down ? -v.u_wall : v.u_wall;
         C2 sv[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) sv[i] = pmul(dec2(e[i]), pset(inv_scale_of<P>()));
-        const C2 rw2 = padd(pset(v.rho_ref), sum9(sv));
-        const C rw[2] = {rw2.x, rw2.y};
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            if ((down && cy(i) == -1) || (!down && cy(i) == 1)) {
-#pragma unroll
-                for (int s = 0; s < 2; ++s) {
-                    const C fi = (s ? sv[i].y : sv[i].x) + wgt<C>(i) * v.rho_ref;
-                    const C back = fi - C(6) * wgt<C>(i) * rw[s] * (C(cx(i)) * uw);
-                    const double dp = (double)(C(cx(i)) * (fi + back));
-                    if (down) red[0] += dp; else red[1] += dp;
-                }
-            }
-        }
+        for (int i = 0; i < 9; ++i) sv[i] = dec2(e[i]);
+        const C2 rw2 = pfma(sum9(sv), pset(inv_scale_of<P>()), pset(v.rho_ref));
+        const C2 dd = pmul(down ? psub(sv[8], sv[7]) : psub(sv[5], sv[6]), pset(inv_scale_of<P>()));
+        const C2 m = psub(pmul(pset(C(2)), dd), pmul(rw2, pset(uw * (C(1) / C(3)))));
+        const double sum = (double)m.x + (double)m.y;
+        if (down) red[0] += sum; else red[1] += sum;
     }
 }
 
@@ -687,7 +683,6 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
     __shared__ __align__(8) uint64_t bars[L::NB];
     __shared__ int s_fail, s_last;
     __shared__ double s_red[L::NT / 32][4];
-    __shared__ int s_wany[L::NT / 32];
     __shared__ uint64_t s_pol[2];   // L2 policies of the block loads and the tile stores
 
     const int tid = threadIdx.x;
@@ -978,8 +973,9 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
         if (!per_lat && (ty_a == 0 || ty_b == d->ntiles_y)) {
             // Wall momentum of an item holding a wall row (only these items'
             // slots are read), in FP64.  FP64 issues at a small fraction of
-            // the FP32 rate, so only the warps that updated a wall site
-            // reduce, and thread 0 adds up just those warps, in warp order.
+            // the FP32 rate and with a long latency, so only the warps that
+            // updated a wall site reduce, and warp 0 adds the warps' sums by
+            // a fixed tree (zero for the others).
             const int lane = tid & 31, warp = tid >> 5;
             const bool mine = __any_sync(0xffffffffu, wall[0] != 0.0 || wall[1] != 0.0);
             if (mine) {
@@ -988,20 +984,19 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
             }
             __syncthreads();   // the previous item's reads of s_red are done
             if (lane == 0) {
-                s_wany[warp] = mine ? 1 : 0;
-                s_red[warp][0] = wall[0];
-                s_red[warp][1] = wall[1];
+                s_red[warp][0] = mine ? wall[0] : 0.0;
+                s_red[warp][1] = mine ? wall[1] : 0.0;
             }
             __syncthreads();
-            if (tid == 0) {
-                double b = 0.0, t = 0.0;
-                for (int w = 0; w < L::NT / 32; ++w)
-                    if (s_wany[w]) {
-                        b += s_red[w][0];
-                        t += s_red[w][1];
-                    }
-                a.slots[2 * it] = b;
-                a.slots[2 * it + 1] = t;
+            if (warp == 0) {
+                double b = lane < L::NT / 32 ? s_red[lane][0] : 0.0;
+                double t = lane < L::NT / 32 ? s_red[lane][1] : 0.0;
+                b = warp_sum(b);
+                t = warp_sum(t);
+                if (lane == 0) {
+                    a.slots[2 * it] = b;
+                    a.slots[2 * it + 1] = t;
+                }
             }
         }
     }
@@ -1026,27 +1021,40 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    for (int l = tid; l < a.nlat; l += L::NT) {
-        const LatDesc<C>* d = &a.lat[l];
-        DevStats* st = d->st;
-        const long long t = st->t;
-        if (!ALLPER && !d->g.periodic) {
-            const int ns = d->nstrips;
-            const int* wi = a.wall_items + d->wall0;
-            const volatile double* vs = a.slots;
-            double sb = 0.0, stp = 0.0;
-            for (int i = 0; i < ns; ++i) sb += vs[2 * wi[i]];
-            for (int i = 0; i < ns; ++i) stp += vs[2 * wi[ns + i] + 1];
-            const long long every = d->stress_every > 0 ? d->stress_every : 1;
-            if (t >= d->stress_t0 && ((t - d->stress_t0) % every) == 0) {
-                st->sum_bot += sb / d->g.nx;
-                st->sum_top += stp / d->g.nx;
-                st->samples += 1;
+    // One warp per lattice.  The wall samples are summed over the strips in
+    // a fixed order -- lane l adds strips l, l + 32, ..., then a butterfly
+    // over the lanes -- so they do not depend on the partition; FP64 has a
+    // long latency on this GPU, so no serial chain runs over the strips.
+    {
+        const int lane = tid & 31;
+        for (int l = tid >> 5; l < a.nlat; l += L::NT / 32) {
+            const LatDesc<C>* d = &a.lat[l];
+            DevStats* st = d->st;
+            const long long t = st->t;
+            if (!ALLPER && !d->g.periodic) {
+                const int ns = d->nstrips;
+                const int* wi = a.wall_items + d->wall0;
+                const volatile double* vs = a.slots;
+                double sb = 0.0, stp = 0.0;
+                for (int i = lane; i < ns; i += 32) {
+                    sb += vs[2 * wi[i]];
+                    stp += vs[2 * wi[ns + i] + 1];
+                }
+                sb = warp_sum(sb);
+                stp = warp_sum(stp);
+                const long long every = d->stress_every > 0 ? d->stress_every : 1;
+                if (lane == 0 && t >= d->stress_t0 && ((t - d->stress_t0) % every) == 0) {
+                    st->sum_bot += sb * d->inv_nx;
+                    st->sum_top += stp * d->inv_nx;
+                    st->samples += 1;
+                }
+            }
+            if (lane == 0) {
+                st->t = t + 1;
+                st->cur ^= 1;
+                st->pull = 1;
             }
         }
-        st->t = t + 1;
-        st->cur ^= 1;
-        st->pull = 1;
     }
     __threadfence();
     if (tid == 0) *a.ticket = 0u;

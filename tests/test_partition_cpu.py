@@ -26,11 +26,13 @@ def lattices(lb, dims, prec="fp32"):
 
 def tile_cost(nx, ny, periodic, tx, sx, ty):
     """The cost model the library documents: a ragged tile 1.04, a tile that
-    writes periodic ghost copies 1.26, an interior tile 1."""
+    writes periodic ghost copies or holds a Couette wall row 1.26, an
+    interior tile 1."""
     x0, y0 = sx * tx, ty * TY
     if not (x0 + tx <= nx and y0 + TY <= ny):
         return 1.04
-    edge = x0 < 3 or x0 + tx > nx - 3 or (periodic and (y0 < 3 or y0 + TY > ny - 3))
+    edge = (x0 < 3 or x0 + tx > nx - 3 or (periodic and (y0 < 3 or y0 + TY > ny - 3))
+            or (not periodic and (y0 == 0 or y0 + TY >= ny)))
     return 1.26 if edge else 1.0
 
 
