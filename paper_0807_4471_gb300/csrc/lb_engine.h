@@ -34,7 +34,7 @@ struct Lattice {
 // One launch of the persistent step kernel over a set of lattices.
 struct Launch {
     int precision;
-    int variant;             // bit 0: all periodic; bit 1: general forcing
+    int variant;             // bit 0: all periodic; bit 1: general forcing; bit 2: 1 - omega = 0
     int spt;                 // sites per thread: tiles of 8 spt rows
     dim3 grid;
     int nitems, seg;

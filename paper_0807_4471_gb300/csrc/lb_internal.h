@@ -132,6 +132,8 @@ struct BatchArgs {
     double* slots;              // [nitems][2] wall-momentum partial sums
     unsigned int* ticket;       // CTA arrival counter of the launch (zero between launches)
     int l2_resident;            // one buffer of all lattices fits in L2: cache-policy hints
+    int early_release;          // kernel variant bit 2 only: a tile's ring slots are refilled
+                                // after its density phase (else after its site phase)
 };
 
 // Observe-mode outputs (the kernel writes FP64 planes of nx*ny values).
@@ -163,7 +165,8 @@ int kernel_block_rows(int precision);
 int kernel_scale_log2(int precision);
 
 // Step: the persistent multi-lattice kernel (args: BatchArgs<C>), variant
-// bit 0 = every lattice periodic, bit 1 = general forcing, spt sites per
+// bit 0 = every lattice periodic, bit 1 = general forcing, bit 2 = 1 - omega
+// rounds to zero for both species (the collision reads no populations), spt sites per
 // thread (tiles of 8 spt rows).  Observe: one lattice, one CTA per 8-row
 // tile (args: StepArgs<C>, tin: tile-box load map).
 cudaError_t launch_step(int precision, const void* args, int variant, int spt, dim3 grid,

@@ -219,19 +219,36 @@ __device__ __forceinline__ C2 dpsi_of(C2 d, const LatVals<C>& v) {
     return pmul(pset(-v.psi_scale), pexpm1(pmul(d, pset(-v.inv_rho0))));
 }
 
+// Momentum j = sum_i c_i f_i of both species from the offsets (sum_i w_i c_i
+// = 0, so the offsets carry all of j), in the compute scale.
+template <int P>
+__device__ __forceinline__ void moments(const typename Prec<P>::C2 h[9], typename Prec<P>::C2& jx,
+                                        typename Prec<P>::C2& jy) {
+    typedef typename Prec<P>::C2 C2;
+    const C2 d57 = psub(h[5], h[7]), d68 = psub(h[6], h[8]);
+    jx = padd(psub(h[1], h[3]), psub(d57, d68));
+    jy = padd(psub(h[2], h[4]), padd(d57, d68));
+    if constexpr (Prec<P>::SCALE_LOG2 != 0) {
+        jx = pmul(jx, pset(inv_scale_of<P>()));
+        jy = pmul(jy, pset(inv_scale_of<P>()));
+    }
+}
+
 // Density and pseudo-potential deviations (rho - rho_ref, Psi - Psi(rho_ref))
-// of both species at one site.
-template <int P, int PS>
+// of both species at one site; with J, also the site's momentum.
+template <int P, int PS, bool J = false>
 __device__ __forceinline__ void cell_dev(const typename Prec<P>::T2* bm,
                                          const typename Prec<P>::T2* b0,
                                          const typename Prec<P>::T2* bp, int y, bool per, int pull,
                                          const Geom& g, const LatVals<typename Prec<P>::C>& v,
-                                         typename Prec<P>::C2& r, typename Prec<P>::C2& q) {
+                                         typename Prec<P>::C2& r, typename Prec<P>::C2& q,
+                                         typename Prec<P>::C2* j = nullptr) {
     typename Prec<P>::C2 h[9];
     load_site<P, PS>(bm, b0, bp, y, per, pull, g, v, h);
     r = sum9(h);
     if constexpr (Prec<P>::SCALE_LOG2 != 0) r = pmul(r, pset(inv_scale_of<P>()));
     q = dpsi_of(r, v);
+    if constexpr (J) moments<P>(h, j[0], j[1]);
 }
 
 // Post-collision offsets of both species (Eq. (1), BGK toward the
@@ -243,21 +260,40 @@ __device__ __forceinline__ void cell_dev(const typename Prec<P>::T2* bm,
 // heq = w (g +- rho c.v) with g = Q + rho (c.v)^2 / 2.  h and out are in
 // the storage scale SC (a power of two); k.omw holds omega SC w per class
 // of |c|^2 and k.omm = 1 - omega.
-template <typename C, typename C2, bool SRC>
+// TAU1: omega = 1 for both species, where h*_i = heq_i and h is not read.
+//
+// TAU1 (omega = 1): h*_i = heq_i, taken per class c of |c_i|^2 as
+//   h*_{i, opp(i)} = E +- kv,  E = T_c + kv (c.v) / 2,  kv = K_c (c.v),
+// with T_c = omega S w_c Q and K_c = omega S w_c rho per site; h is not read.
+template <typename C, typename C2, bool SRC, bool TAU1 = false>
 __device__ __forceinline__ void collide(const C2 h[9], C2 out[9], C2 drho, C2 rho, C2 vx, C2 vy,
                                         const Coef<C>& k, C2 Fx, C2 Fy, C SC) {
     const C2 Q = pfma(pmul(rho, pset(C(-1) / C(6))), pfma(vx, vx, pmul(vy, vy)), drho);
-    out[0] = pfma(k.omw[0], Q, pmul(k.omm, h[0]));
+    out[0] = TAU1 ? pmul(k.omw[0], Q) : pfma(k.omw[0], Q, pmul(k.omm, h[0]));
+    C2 T[2], K[2];
+    if (TAU1) {
+        T[0] = pmul(k.omw[1], Q);
+        T[1] = pmul(k.omw[2], Q);
+        K[0] = pmul(k.omw[1], rho);
+        K[1] = pmul(k.omw[2], rho);
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int i = q == 0 ? 1 : (q == 1 ? 2 : (q == 2 ? 5 : 6));   // c.v = vx, vy, vx+vy, vy-vx
         const int j = opp(i);
         const C2 cv = q == 0 ? vx : (q == 1 ? vy : (q == 2 ? padd(vx, vy) : psub(vy, vx)));
-        const C2 ow = k.omw[q < 2 ? 1 : 2];
-        const C2 rv = pmul(rho, cv);
-        const C2 g = pfma(rv, pmul(cv, pset(C(0.5))), Q);
-        out[i] = pfma(ow, padd(g, rv), pmul(k.omm, h[i]));
-        out[j] = pfma(ow, psub(g, rv), pmul(k.omm, h[j]));
+        if (TAU1) {
+            const C2 kv = pmul(K[q >> 1], cv);
+            const C2 E = pfma(kv, pmul(cv, pset(C(0.5))), T[q >> 1]);
+            out[i] = padd(E, kv);
+            out[j] = psub(E, kv);
+        } else {
+            const C2 ow = k.omw[q < 2 ? 1 : 2];
+            const C2 rv = pmul(rho, cv);
+            const C2 g = pfma(rv, pmul(cv, pset(C(0.5))), Q);
+            out[i] = pfma(ow, padd(g, rv), pmul(k.omm, h[i]));
+            out[j] = pfma(ow, psub(g, rv), pmul(k.omm, h[j]));
+        }
         if (SRC) {
             const C w3 = C(3) * SC * wgt<C>(i);
             const C2 S = pmul(pset(w3), pfma(pset(C(cx(i))), Fx, pmul(pset(C(cy(i))), Fy)));
@@ -277,8 +313,9 @@ __device__ __forceinline__ void collide(const C2 h[9], C2 out[9], C2 drho, C2 rh
 //                              + K(2,|dy|) (q(2) + q(-2))].
 // (The reference values of Psi and rho drop out: sum_d K(d) d = 0.)  The
 // differences and sums of a row are shared by every site whose stencil
-// holds the row; each site adds its rows in the order dy = -2 .. 2, so a
-// site's force is the same whether it shares rows with another or not.
+// holds the row; each site adds its rows in a fixed order (x: dy = -2 .. 2;
+// y: the rows above minus the rows below, each part in the order of dy), so
+// a site's force is the same whether it shares rows with another or not.
 
 // The shared quantities of one stencil row, p at the site's column.
 template <typename C2>
@@ -314,29 +351,32 @@ __device__ __forceinline__ Row3<C2> row3(const C2* p) {
 // weights KC = {K(1), K(2), K(5), 2K(4), 2K(5), 2K(8)}: x takes
 // K(1,|dy|) = K(1), K(2), K(5) and 2K(2,|dy|) = 2K(4), 2K(5), 2K(8) for
 // |dy| = 0, 1, 2; y takes {K(1), K(2), K(5)} for |dy| = 1 and
-// {2K(4), 2K(5), 2K(8)} for |dy| = 2.
+// {2K(4), 2K(5), 2K(8)} for |dy| = 2.  The y sum is kept as two chains,
+// rows below the site (fyn: dy = -2, -1) and above it (fyp: dy = 1, 2),
+// each started by its first row; fy = fyp - fyn.
 template <typename C, typename C2>
 __device__ __forceinline__ void like_row(int dy, const Row5<C2>& r, const Coef<C>& k, C2& fx,
-                                         C2& fy) {
+                                         C2& fyp, C2& fyn) {
     const int a = dy < 0 ? -dy : dy;
     fx = pfma(a == 0 ? k.KC[0] : (a == 1 ? k.KC[1] : k.KC[2]), r.d1, fx);
     fx = pfma(a == 0 ? k.KC[3] : (a == 1 ? k.KC[4] : k.KC[5]), r.d2, fx);
     if (a != 0) {
-        C2 t = pmul(a == 1 ? k.KC[0] : k.KC[3], r.q0);
+        C2& t = dy > 0 ? fyp : fyn;
+        const C2 K0 = a == 1 ? k.KC[0] : k.KC[3];
+        t = (dy == -2 || dy == 1) ? pmul(K0, r.q0) : pfma(K0, r.q0, t);
         t = pfma(a == 1 ? k.KC[1] : k.KC[4], r.s1, t);
         t = pfma(a == 1 ? k.KC[2] : k.KC[5], r.s2, t);
-        fy = dy > 0 ? padd(fy, t) : psub(fy, t);
     }
 }
-// Cross-species row at offset dy (|dy| <= 1), D2Q9 weights WC = {w(1), w(2)}.
+// Cross-species row at offset dy (|dy| <= 1), D2Q9 weights WC = {w(1), w(2)};
+// qy is taken as qyp - qyn, the rows above and below.
 template <typename C, typename C2>
 __device__ __forceinline__ void cross_row(int dy, const Row3<C2>& r, const Coef<C>& k, C2& qx,
-                                          C2& qy) {
+                                          C2& qyp, C2& qyn) {
     qx = pfma(dy == 0 ? k.WC[0] : k.WC[1], r.e, qx);
     if (dy != 0) {
-        C2 u = pmul(k.WC[0], r.q0);
-        u = pfma(k.WC[1], r.t, u);
-        qy = dy > 0 ? padd(qy, u) : psub(qy, u);
+        C2& u = dy > 0 ? qyp : qyn;
+        u = pfma(k.WC[1], r.t, pmul(k.WC[0], r.q0));
     }
 }
 
@@ -350,15 +390,16 @@ __device__ __forceinline__ void force_sums(const C2* ps, const C2* rr, const Coe
                                            C2 fy[NS], C2 qx[NS], C2 qy[NS], C2 dpsi[NS],
                                            C2 drho[NS]) {
     const C2 z = pset(C(0));
+    C2 fyp[NS], fyn[NS], qyp[NS], qyn[NS];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) fx[s] = fy[s] = qx[s] = qy[s] = z;
+    for (int s = 0; s < NS; ++s) fx[s] = qx[s] = z;
 #pragma unroll
     for (int r = 0; r < NS + 4; ++r) {
         const Row5<C2> w = row5(ps + r * RXS);
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             const int dy = r - 2 - s;
-            if (dy >= -2 && dy <= 2) like_row(dy, w, k, fx[s], fy[s]);
+            if (dy >= -2 && dy <= 2) like_row(dy, w, k, fx[s], fyp[s], fyn[s]);
             if (dy == 0) dpsi[s] = w.q0;
         }
     }
@@ -368,9 +409,14 @@ __device__ __forceinline__ void force_sums(const C2* ps, const C2* rr, const Coe
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             const int dy = r - 2 - s;
-            if (dy >= -1 && dy <= 1) cross_row(dy, w, k, qx[s], qy[s]);
+            if (dy >= -1 && dy <= 1) cross_row(dy, w, k, qx[s], qyp[s], qyn[s]);
             if (dy == 0) drho[s] = w.q0;
         }
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        fy[s] = psub(fyp[s], fyn[s]);
+        qy[s] = psub(qyp[s], qyn[s]);
     }
 }
 
@@ -390,6 +436,18 @@ __device__ __forceinline__ void st_pair(T2* p, T2 v, uint64_t pol) {   // 16-bit
                  "r"(*reinterpret_cast<const uint32_t*>(&v)), "l"(pol));
 }
 
+// Random word of site (x, y) for the stochastic rounding of its stored
+// pairs, from key, the hash of the lattice's step: sites (x, 2m) and
+// (x, 2m + 1) share one hash of (x, 2m) -- the second site takes it times an
+// odd constant (a bijection, so each word is uniform) -- whichever thread
+// updates them.
+__device__ __forceinline__ uint32_t sr_hash(uint32_t key, int x, int y, int nx) {
+    return hash32(key ^ (uint32_t)((y & ~1) * nx + x));
+}
+__device__ __forceinline__ uint32_t sr_word(uint32_t h, int y) {
+    return (y & 1) ? h * 0x2c1b3c6du : h;
+}
+
 // Where a site update sends its result.
 enum SiteSink : int { SINK_STAGE = 0, SINK_GLOBAL = 1 };
 template <typename T2>
@@ -400,7 +458,7 @@ struct SiteOut {
     long long gdy;         // SINK_GLOBAL: offset of the periodic image in y (0: none)
     int gdx;               // SINK_GLOBAL: offset of the periodic image in x (0: none)
     uint64_t pol;          // SINK_GLOBAL: L2 policy of the stores
-    uint32_t key;          // stochastic rounding: hash of the lattice's step
+    uint32_t rbits;        // stochastic rounding: the site's random word (sr_word)
     int valid;             // 0: a site beyond the lattice, computed only to keep
                            // the site updates of a thread free of branches:
                            // its global stores and non-finite flag are dropped
@@ -412,29 +470,32 @@ struct SiteOut {
 // One lattice site, given its force sums: moments from its pulled
 // populations, the force of Eq. (2), and either the forced BGK collision and
 // write-back (OBS = false) or the observables (OBS = true).  Both species are
-// carried as (A, B) pairs throughout.
-template <int P, bool OBS, bool GEN, int PS, int SINK>
+// carried as (A, B) pairs throughout.  TAU1 (omega = 1 for both species,
+// OBS = false): the collision needs the populations only through j, which the
+// caller passes in jg = {jx, jy}; bm, b0 and bp are not read.
+template <int P, bool OBS, bool GEN, int PS, int SINK, bool TAU1 = false>
 __device__ __forceinline__ void site_update(
     const typename Prec<P>::T2* bm, const typename Prec<P>::T2* b0,
     const typename Prec<P>::T2* bp, typename Prec<P>::C2 fxl, typename Prec<P>::C2 fyl,
     typename Prec<P>::C2 qx, typename Prec<P>::C2 qy, typename Prec<P>::C2 dpsi,
     typename Prec<P>::C2 drho, int x, int y, bool per, int pull, const Geom& g,
     const LatVals<typename Prec<P>::C>& v, const Coef<typename Prec<P>::C>& k,
-    const SiteOut<typename Prec<P>::T2>& o, double red[4], bool& bad) {
+    const SiteOut<typename Prec<P>::T2>& o, double red[4], bool& bad,
+    const typename Prec<P>::C2* jg = nullptr) {
     typedef typename Prec<P>::T2 T2;
     typedef typename Prec<P>::C C;
     typedef typename Prec<P>::C2 C2;
+    static_assert(!(TAU1 && OBS), "the observables read the populations");
     C2 h[9];
-    load_site<P, PS>(bm, b0, bp, y, per, pull, g, v, h);
-    const C2 rho = padd(pset(v.rho_ref), drho);
-    // sum_i w_i c_i = 0, so the offsets carry all of j
-    const C2 d57 = psub(h[5], h[7]), d68 = psub(h[6], h[8]);
-    C2 jx = padd(psub(h[1], h[3]), psub(d57, d68));
-    C2 jy = padd(psub(h[2], h[4]), padd(d57, d68));
-    if constexpr (Prec<P>::SCALE_LOG2 != 0) {
-        jx = pmul(jx, pset(inv_scale_of<P>()));
-        jy = pmul(jy, pset(inv_scale_of<P>()));
+    C2 jx, jy;
+    if constexpr (TAU1) {
+        jx = jg[0];
+        jy = jg[1];
+    } else {
+        load_site<P, PS>(bm, b0, bp, y, per, pull, g, v, h);
+        moments<P>(h, jx, jy);
     }
+    const C2 rho = padd(pset(v.rho_ref), drho);
     if (o.valid && !(isfinite(rho.x) && isfinite(rho.y))) bad = true;
 
     // Eq. (2): F_s = -Psi_s(r) sum_d K_s(d) d Psi_s(r + d)
@@ -482,8 +543,10 @@ __device__ __forceinline__ void site_update(
     // u' = sum_s (j_s/tau_s) / sum_s (rho_s/tau_s); shift u_s = u' + tau_s F_s/rho_s;
     // carried as v = 3u.  (Selects, not branches: an empty site has u' = 0
     // and no shift.)
+    // (TAU1: omega = 1 exactly, and the products are the values themselves)
     const C2 om = pair(k.omega[0], k.omega[1]);
-    const C2 ro = pmul(rho, om), jxo = pmul(jx, om), jyo = pmul(jy, om);
+    const C2 ro = TAU1 ? rho : pmul(rho, om), jxo = TAU1 ? jx : pmul(jx, om),
+             jyo = TAU1 ? jy : pmul(jy, om);
     const C den = ro.x + ro.y;
     const C inv3 = den != C(0) ? C(3) * recip(den) : C(0);
     const C2 vp = pair((jxo.x + jxo.y) * inv3, (jyo.x + jyo.y) * inv3);
@@ -497,13 +560,13 @@ __device__ __forceinline__ void site_update(
     }
     C2 hs[9];
     if (source)
-        collide<C, C2, true>(h, hs, drho, rho, vx, vy, k, Fx, Fy, scale_of<P>());
+        collide<C, C2, true, TAU1>(h, hs, drho, rho, vx, vy, k, Fx, Fy, scale_of<P>());
     else
-        collide<C, C2, false>(h, hs, drho, rho, vx, vy, k, Fx, Fy, scale_of<P>());
+        collide<C, C2, false, TAU1>(h, hs, drho, rho, vx, vy, k, Fx, Fy, scale_of<P>());
     T2 e[9];
     if constexpr (sizeof(T2) == 4) {
         if (k.sr) {   // half formats: random bits from (site, step), one word per pair
-            const uint32_t r = hash32(o.key ^ (uint32_t)(y * g.nx + x));
+            const uint32_t r = o.rbits;
 #pragma unroll
             for (int i = 0; i < 9; ++i) e[i] = enc2_sr<T2>(hs[i], r * sr_mult(i));
         } else {
@@ -671,6 +734,9 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
     typedef typename L::C2 C2;
     constexpr bool ALLPER = (V & 1) != 0;
     constexpr bool GEN = (V & 2) != 0;
+    // omega = 1 for both species: the site phase needs the populations only
+    // through j, which the density phase computes beside rho and Psi
+    constexpr bool TAU1 = (V & 4) != 0;
     constexpr bool STAGED = L::STAGED;   // output through the staging tile
     constexpr int PS = L::TYB * L::BX;   // plane stride in a block slot (pairs)
     extern __shared__ unsigned char smem_raw[];
@@ -699,6 +765,26 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
     // window column and block row of this thread (both phases)
     const int t_lx = tid % L::RX, t_j = tid / L::RX;
     static_assert(L::NT == L::RX * L::TYB && L::TY >= 4, "one window column per thread and block row");
+    // Rows of the density phase: thread row t_j computes the new window rows
+    // 4 + SPT t_m + c, c < SPT, which hold its own sites (window rows
+    // 2 + SPT t_j + c) for t_j >= 2 / SPT; the first 2 / SPT thread rows,
+    // whose sites sit in the two rows carried over from the previous tile,
+    // compute the last two rows -- the next tile's first sites, theirs again.
+    // So every thread's sites were computed by the thread itself, in this
+    // tile or (first thread rows) in the previous one, and their momenta can
+    // stay in its registers (TAU1).
+    constexpr int kCarry = 2 / SPT;   // thread rows whose sites are carried rows
+    static_assert(2 % SPT == 0, "two carried rows per tile");
+    const int t_m = (t_j + L::TYB - kCarry) % L::TYB;
+    const bool t_carry = t_j < kCarry;
+    // Columns likewise: window column w holds lattice column x0 - 2 + w and
+    // site column lx is window column lx + 2, so thread t_lx computes window
+    // column (t_lx + 2) mod RX -- its own site column, and for the RX - TX
+    // threads without a site the halo columns.
+    const int t_w = (t_lx + 2) % L::RX;
+    // TAU1: momenta (jx, jy) of this thread's sites computed in the previous
+    // tile (used by the first thread rows) and in this one
+    C2 jprev[SPT][2];
     auto slot = [&](int pos) { return reinterpret_cast<T2*>(smem + (pos % L::NB) * L::SLOT_BYTES); };
     const int it_end = a.cta_items[blockIdx.x + 1];
 
@@ -751,6 +837,15 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
     if (tid == 0) p_load();
     if (tid == 0)
         while (p_pos < L::NB && issue_next()) {}
+    int ty_b = 0, ty = 0;   // the consumer's item end and tile (read by release)
+    // Producer: the tile whose first block is at position q is done with
+    // its blocks before the next tile's first one (all of them at an item's
+    // last tile): refill those slots.
+    auto release = [&](int q) {
+        const int released = (ty + 1 < ty_b) ? q + SPT : q + SPT + 1;
+        fence_proxy_async();   // generic reads of freed slots before async writes
+        while (p_pos < released + L::NB && issue_next()) {}
+    };
 
     bool bad = false;
     int c_pos = 0;   // ring position of the current item's first block
@@ -759,7 +854,7 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
         const LatDesc<C>* d = &a.lat[w.x];
         const int x0 = w.y * L::TX;
         const int ty_a = w.z;
-        const int ty_b = w.w;
+        ty_b = w.w;
         const Geom g = d->g;
         const LatVals<C> v = d->v;
         const bool per_lat = ALLPER || g.periodic;
@@ -772,7 +867,7 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
         // ring slot and phase parity of the tile's first block, kept as the
         // tiles advance
         int qm = c_pos % L::NB, qph = (c_pos / L::NB) & 1;
-        for (int ty = ty_a; ty < ty_b; ++ty) {
+        for (ty = ty_a; ty < ty_b; ++ty) {
             const int q = c_pos + SPT * (ty - ty_a);   // this tile uses blocks q .. q + SPT
             // Each thread sees the blocks land itself (the first block of a
             // tile after an item's first was seen as the previous tile's
@@ -808,31 +903,35 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
             auto tile_body = [&](auto wall_tag) -> bool {
                 constexpr bool W = decltype(wall_tag)::value;
                 const bool per = !W || per_lat;
+                C2 jn[SPT][2];   // TAU1: momenta of this thread's new rows
                 // Phase 2: window row k holds lattice row y0 - 2 + k (padded row
-                // y0 + 1 + k).  Rows 4 .. TY + 3 are new: thread row t_j computes
-                // rows 4 + SPT t_j + c, c < SPT.  Rows 0 .. 3 are the previous
+                // y0 + 1 + k).  Rows 4 .. TY + 3 are new: thread (t_lx, t_j)
+                // computes rows 4 + SPT t_m + c, c < SPT, of window column t_w
+                // (the thread's own sites, see t_m).  Rows 0 .. 3 are the previous
                 // tile's rows TY .. TY + 3, carried forward by the threads that
                 // own those before they overwrite them, or at an item's first
                 // tile computed from block q.  No other thread touches these
                 // cells in this phase.
                 {
-                    const int bc = t_lx - 2 + L::GX;   // pair column in the block
+                    const int bc = t_w - 2 + L::GX;   // pair column in the block
                     // rows 0 .. 3: carried forward, or computed at an item's first
                     // tile, before this thread's new rows overwrite their sources
+                    // (rows 2 and 3, at an item's first tile, by the thread rows
+                    // whose sites they are: their momenta start the carry)
     #pragma unroll
                     for (int c = 0; c < SPT; ++c) {
-                        const int k = 4 + SPT * t_j + c;
+                        const int k = 4 + SPT * t_m + c;
                         const int kk = k - L::TY;
                         if (kk >= 0) {
                             if (ty == ty_a) {
                                 C2 r, p;
-                                cell_dev<P, PS>(brow(kk, bc), brow(kk + 1, bc), brow(kk + 2, bc),
-                                                y0 - 2 + kk, per, pull, g, v, r, p);
-                                win_r[kk * L::RX + t_lx] = r;
-                                win_p[kk * L::RX + t_lx] = p;
+                                cell_dev<P, PS, TAU1>(brow(kk, bc), brow(kk + 1, bc), brow(kk + 2, bc),
+                                                      y0 - 2 + kk, per, pull, g, v, r, p, jprev[c]);
+                                win_r[kk * L::RX + t_w] = r;
+                                win_p[kk * L::RX + t_w] = p;
                             } else {
-                                win_r[kk * L::RX + t_lx] = win_r[k * L::RX + t_lx];
-                                win_p[kk * L::RX + t_lx] = win_p[k * L::RX + t_lx];
+                                win_r[kk * L::RX + t_w] = win_r[k * L::RX + t_w];
+                                win_p[kk * L::RX + t_w] = win_p[k * L::RX + t_w];
                             }
                         }
                     }
@@ -843,12 +942,12 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
                     // mirror below overwrites the two rows past each wall.
     #pragma unroll
                     for (int c = 0; c < SPT; ++c) {
-                        const int k = 4 + SPT * t_j + c;
+                        const int k = 4 + SPT * t_m + c;
                         C2 r, p;
-                        cell_dev<P, PS>(brow(k, bc), brow(k + 1, bc), brow(k + 2, bc), y0 - 2 + k, per,
-                                        pull, g, v, r, p);
-                        win_r[k * L::RX + t_lx] = r;
-                        win_p[k * L::RX + t_lx] = p;
+                        cell_dev<P, PS, TAU1>(brow(k, bc), brow(k + 1, bc), brow(k + 2, bc), y0 - 2 + k,
+                                              per, pull, g, v, r, p, jn[c]);
+                        win_r[k * L::RX + t_w] = r;
+                        win_p[k * L::RX + t_w] = p;
                     }
                 }
                 // mirror the deviations about the halfway walls, in the tiles whose
@@ -870,6 +969,11 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
                 if (STAGED && tid == kStoreThread) bulk_wait_read();   // previous bulk store has read the staging tile
                 __syncthreads();
                 if (s_fail) return false;
+                if constexpr (TAU1) {
+                    // The site phase reads no populations: the tile's blocks
+                    // before the next tile's first one are free already.
+                    if (a.early_release && tid == 0) release(q);
+                }
 
                 // Phase 3: SPT sites per thread (lx < TX): sites (x0 + t_lx,
                 // y0 + SPT t_j + s), whose stencil rows y - 2 .. y + 2 are window
@@ -884,7 +988,9 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
                         force_sums<SPT, L::RX>(win_p + ly * L::RX + lx + 2,
                                                win_r + ly * L::RX + lx + 2, a.k, fx, fy, qx, qy, dp, dr);
                         SiteOut<T2> o;
-                        o.key = key;
+                        o.rbits = 0u;
+                        uint32_t srh = 0u;   // the shared hash of this thread's sites
+                        if constexpr (sizeof(T2) == 4) srh = sr_hash(key, x, y, g.nx);
                         o.obs = OBS_NONE;
                         o.valid = 1;
                         if constexpr (!STAGED) {
@@ -899,6 +1005,10 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
                         for (int s = 0; s < SPT; ++s) {
                             const int ys = y + s;
                             o.valid = s == 0 || ys < g.ny;
+                            if constexpr (sizeof(T2) == 4) {
+                                // SPT = 2: y is even (tile rows are multiples of 16)
+                                o.rbits = sr_word(SPT == 2 ? srh : sr_hash(key, x, ys, g.nx), ys);
+                            }
                             if constexpr (STAGED) {
                                 o.stage = stage + L::stage_off(ly + s, lx);
                             } else {
@@ -908,16 +1018,32 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
                                         : (ys >= g.ny - 3 ? -(long long)g.ny * g.pitch : 0);
                             }
                             double wr[4] = {0.0, 0.0, 0.0, 0.0};
-                            site_update<P, false, GEN, PS, STAGED ? SINK_STAGE : SINK_GLOBAL>(
-                                brow(ly + s + 2, bc), brow(ly + s + 3, bc), brow(ly + s + 4, bc), fx[s],
-                                fy[s], qx[s], qy[s], dp[s], dr[s], x, ys, per, pull, g, v, a.k, o, wr,
-                                bad);
+                            if constexpr (TAU1) {
+                                C2 js[2];
+                                js[0] = t_carry ? jprev[s][0] : jn[s][0];
+                                js[1] = t_carry ? jprev[s][1] : jn[s][1];
+                                site_update<P, false, GEN, PS, STAGED ? SINK_STAGE : SINK_GLOBAL, true>(
+                                    nullptr, nullptr, nullptr, fx[s], fy[s], qx[s], qy[s], dp[s], dr[s],
+                                    x, ys, per, pull, g, v, a.k, o, wr, bad, js);
+                            } else {
+                                site_update<P, false, GEN, PS, STAGED ? SINK_STAGE : SINK_GLOBAL>(
+                                    brow(ly + s + 2, bc), brow(ly + s + 3, bc), brow(ly + s + 4, bc),
+                                    fx[s], fy[s], qx[s], qy[s], dp[s], dr[s], x, ys, per, pull, g, v,
+                                    a.k, o, wr, bad);
+                            }
                             if (!per && (ys == 0 || ys == g.ny - 1)) {   // FP64: wall rows only
                                 wall[0] += wr[0];
                                 wall[1] += wr[1];
                             }
                         }
                         if constexpr (STAGED) fence_proxy_async();   // staging writes before the bulk store
+                    }
+                }
+                if constexpr (TAU1) {
+#pragma unroll
+                    for (int c = 0; c < SPT; ++c) {
+                        jprev[c][0] = jn[c][0];
+                        jprev[c][1] = jn[c][1];
                     }
                 }
                 return true;
@@ -946,12 +1072,7 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
                     bulk_commit();
                 }
             }
-            if (tid == 0) {
-                // blocks before the next tile's first block are free
-                const int released = (ty + 1 < ty_b) ? q + SPT : q + SPT + 1;
-                fence_proxy_async();   // generic reads of freed slots before async writes
-                while (p_pos < released + L::NB && issue_next()) {}
-            }
+            if (!(TAU1 && a.early_release) && tid == 0) release(q);
             if constexpr (STAGED) {
                 // only tiles within 3 sites of an edge write periodic ghost copies
                 const bool edge = x0 < 3 || x0 + L::TX > g.nx - 3 ||
@@ -1142,7 +1263,7 @@ __global__ void __launch_bounds__(Layout<P>::NT)
                                  qx, qy, dp, dr);
             SiteOut<T2> o;
             o.stage = nullptr;
-            o.key = 0u;
+            o.rbits = 0u;
             o.valid = 1;
             o.obs = a.obs;
             o.obs_out = a.obs_out;
@@ -1300,12 +1421,20 @@ static cudaError_t configure_all() {
     opt(k_step<P, 1, 1>, L::SMEM);
     opt(k_step<P, 2, 1>, L::SMEM);
     opt(k_step<P, 3, 1>, L::SMEM);
+    opt(k_step<P, 4, 1>, L::SMEM);
+    opt(k_step<P, 5, 1>, L::SMEM);
+    opt(k_step<P, 6, 1>, L::SMEM);
+    opt(k_step<P, 7, 1>, L::SMEM);
     if constexpr (Prec<P>::NB2 > 0) {
         typedef Layout<P, 2> L2;
         opt(k_step<P, 0, 2>, L2::SMEM);
         opt(k_step<P, 1, 2>, L2::SMEM);
         opt(k_step<P, 2, 2>, L2::SMEM);
         opt(k_step<P, 3, 2>, L2::SMEM);
+        opt(k_step<P, 4, 2>, L2::SMEM);
+        opt(k_step<P, 5, 2>, L2::SMEM);
+        opt(k_step<P, 6, 2>, L2::SMEM);
+        opt(k_step<P, 7, 2>, L2::SMEM);
     }
     opt(k_observe<P, 2>, L::SMEM_OBS);
     opt(k_observe<P, 3>, L::SMEM_OBS);
@@ -1353,11 +1482,15 @@ static cudaError_t launch_step_shape(const BatchArgs<typename Prec<P>::C>& a, in
     cfg.attrs = at;
     cfg.numAttrs = pdl_enabled() ? 1 : 0;
     cudaError_t e;
-    switch (variant & 3) {
+    switch (variant & 7) {
         case 0: e = cudaLaunchKernelEx(&cfg, k_step<P, 0, SPT>, a); break;
         case 1: e = cudaLaunchKernelEx(&cfg, k_step<P, 1, SPT>, a); break;
         case 2: e = cudaLaunchKernelEx(&cfg, k_step<P, 2, SPT>, a); break;
-        default: e = cudaLaunchKernelEx(&cfg, k_step<P, 3, SPT>, a); break;
+        case 3: e = cudaLaunchKernelEx(&cfg, k_step<P, 3, SPT>, a); break;
+        case 4: e = cudaLaunchKernelEx(&cfg, k_step<P, 4, SPT>, a); break;
+        case 5: e = cudaLaunchKernelEx(&cfg, k_step<P, 5, SPT>, a); break;
+        case 6: e = cudaLaunchKernelEx(&cfg, k_step<P, 6, SPT>, a); break;
+        default: e = cudaLaunchKernelEx(&cfg, k_step<P, 7, SPT>, a); break;
     }
     return e != cudaSuccess ? e : cudaGetLastError();
 }

@@ -172,13 +172,16 @@ __device__ __forceinline__ float recip(float v) {
 // 16-bit head and a tail so that k * head is exact) and
 // expm1(x) = 2^k expm1(r) + (2^k - 1), with expm1(r) from its Taylor series
 // through r^7 / 7! (truncation below 1.6e-8 relative on |r| <= ln2 / 2).
-// Relative error about 2 ulp; a NaN argument gives NaN.  2^k is assembled
-// in the exponent field, k clamped to the normal range.
+// Relative error about 2 ulp; a NaN argument gives NaN.  k is the integer
+// nearest x / ln2, for x clamped to [-87, 88] (so that 2^k is a normal
+// number, k in [-126, 127]): adding 1.5 2^23 to x log2(e) rounds it to an
+// integer held in the low mantissa bits, which also give 2^k's exponent
+// field by one shift.
 __device__ __forceinline__ double2 pexpm1(double2 v) { return make_double2(expm1(v.x), expm1(v.y)); }
 __device__ __forceinline__ float2 pexpm1(float2 x) {
-    const float2 kr = pmul(x, pset(1.44269504088896341f));
-    const float2 k = make_float2(fminf(fmaxf(rintf(kr.x), -126.0f), 127.0f),
-                                 fminf(fmaxf(rintf(kr.y), -126.0f), 127.0f));
+    const float2 xc = make_float2(fminf(fmaxf(x.x, -87.0f), 88.0f), fminf(fmaxf(x.y, -87.0f), 88.0f));
+    const float2 kt = pfma(xc, pset(1.44269504088896341f), pset(12582912.0f));
+    const float2 k = padd(kt, pset(-12582912.0f));
     float2 r = pfma(k, pset(-0.693145751953125f), x);
     r = pfma(k, pset(-1.42860676533018700e-06f), r);
     float2 t = pset(1.0f / 5040.0f);
@@ -189,8 +192,10 @@ __device__ __forceinline__ float2 pexpm1(float2 x) {
     t = pfma(t, r, pset(0.5f));
     t = pfma(t, r, pset(1.0f));
     const float2 p = pmul(t, r);
-    const float2 s = make_float2(__int_as_float(((int)k.x + 127) << 23),
-                                 __int_as_float(((int)k.y + 127) << 23));
+    // kt's bits are those of 1.5 2^23 plus k, and 1.5 2^23 << 23 vanishes
+    // in 32 bits: (kt << 23) + (127 << 23) is the exponent field of 2^k
+    const float2 s = make_float2(__uint_as_float((__float_as_uint(kt.x) << 23) + 0x3F800000u),
+                                 __uint_as_float((__float_as_uint(kt.y) << 23) + 0x3F800000u));
     return pfma(s, p, padd(s, pset(-1.0f)));
 }
 __device__ __forceinline__ double csin(double v) { return sin(v); }

@@ -189,6 +189,39 @@ def test_fp32_ragged(lb, O, nx, ny, boundary):
     g.close()
 
 
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp16", 5e-3)])
+@pytest.mark.parametrize("boundary", [0, 1])
+def test_general_relaxation_times(lb, O, prec, tol, boundary):
+    """tau_A != 1: the collision keeps the (1 - omega) h term and reads the
+    pulled populations in the site phase (the tau = 1 path, which every other
+    case here takes, does not); 20 steps against the oracle."""
+    m = model(100, 27, boundary=boundary, u_wall=0.03 if boundary else 0.0, tau=(0.8, 1.0))
+    P, f, _, g = run_both(lb, O, m, 20, precision=prec, seed=4)
+    ra, rb, _, _ = O.fields(P, f)
+    ga, gb, _, _ = g.fields()
+    err = max(rel_err(ga, ra), rel_err(gb, rb))
+    print(f"{prec} tau (0.8, 1.0), boundary {boundary}: 20-step relative error {err:.3e}")
+    assert err < tol
+    if prec == "fp32":
+        assert rel_err(gpu_pops_as_oracle(g.populations()), f) < tol
+    g.close()
+
+
+def test_tau1_path_agrees_with_general_path(lb):
+    """tau = 1 (the collision without the populations) against tau = 1 +
+    2^-20, where 1 - omega is 2^-20 in FP32 and the general collision runs:
+    the two differ by that relaxation-time change alone."""
+    res = []
+    for tau in (1.0, 1.0 + 2.0 ** -20):
+        m = model(130, 40, boundary=1, u_wall=0.02, tau=(tau, tau))
+        g = lb.Lattice(gpu_params(lb, m, "fp32")).init_seeded(6)
+        g.step(30)
+        res.append(g.populations())
+        g.close()
+    assert not np.array_equal(res[0], res[1])
+    assert rel_err(res[1], res[0]) < 1e-5
+
+
 def test_fp32_full_size_sweep_lattice(lb, O):
     """At the 512^2 size of the rho0 sweep, in the bench's launch
     configuration: one step against the oracle element by element, and mass

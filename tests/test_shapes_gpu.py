@@ -55,7 +55,7 @@ def test_single_lattice_tile_shapes_bitwise(lb, prec, dims):
         assert s8[key] == s16[key], key
 
 
-@pytest.mark.parametrize("variant", ["accel", "source", "tau"])
+@pytest.mark.parametrize("variant", ["accel", "source", "tau", "tau_fp16_couette"])
 def test_tile_shapes_bitwise_with_forcing(lb, variant):
     if variant == "accel":
         m = model(96, 40, boundary=1, u_wall=0.01, g_x=1e-4, kolmo_amp=2e-4, kolmo_k=1.0)
@@ -63,10 +63,13 @@ def test_tile_shapes_bitwise_with_forcing(lb, variant):
         c = model(96, 40)
         m = model(96, 40, force_scheme=1, Ga=tuple(0.5 * v for v in c["Ga"]),
                   Gr=tuple(0.5 * v for v in c["Gr"]))
-    else:
+    elif variant == "tau":
         m = model(96, 40, tau=(1.0, 0.8))
-    f8, s8 = run_single(lb, m, "fp32", 8, 3, 41)
-    f16, s16 = run_single(lb, m, "fp32", 16, 3, 41)
+    else:
+        m = model(130, 40, boundary=1, u_wall=0.01, init_shear=1, tau=(0.9, 0.8))
+    prec = "fp16" if variant == "tau_fp16_couette" else "fp32"
+    f8, s8 = run_single(lb, m, prec, 8, 3, 41)
+    f16, s16 = run_single(lb, m, prec, 16, 3, 41)
     assert np.array_equal(f8, f16)
     for key in STRESS_KEYS:
         assert s8[key] == s16[key], key
