@@ -99,9 +99,10 @@ static Geom make_geom(const lb_params* p) {
     return g;
 }
 
-// Device region of one lattice: stats, observe slots, two buffers.
+// Device region of one lattice: stats, observe slots, wall columns, two
+// buffers.
 struct Region {
-    size_t stats, slots, f0, f1, total, fbytes;
+    size_t stats, slots, wallx, f0, f1, total, fbytes;
 };
 static Region region_layout(const lb_params* p) {
     Geom g = make_geom(p);
@@ -113,6 +114,10 @@ static Region region_layout(const lb_params* p) {
     off = align_up(off + sizeof(DevStats), kAlign);
     r.slots = off;
     off = align_up(off + sizeof(double) * 4 * ntiles, kAlign);
+    // the step's wall-momentum pair of every wall site (bottom row, then top
+    // row), in the compute precision (at most two doubles)
+    r.wallx = off;
+    off = align_up(off + (size_t)2 * (size_t)p->nx * 2 * sizeof(double), kAlign);
     r.fbytes = align_up((size_t)18 * (size_t)g.plane * (size_t)kernel_elem_bytes(p->precision), kAlign);
     r.f0 = off;
     off += r.fbytes;
@@ -240,6 +245,7 @@ lb_status lattice_setup(Lattice& L, const lb_params* p, char* region) {
     L.region = region;
     L.st = reinterpret_cast<DevStats*>(region + r.stats);
     L.slots = reinterpret_cast<double*>(region + r.slots);
+    L.wallx = region + r.wallx;
     L.fbuf[0] = region + r.f0;
     L.fbuf[1] = region + r.f1;
     L.fbytes = r.fbytes;
@@ -322,6 +328,7 @@ static void fill_desc(LatDesc<C>& d, const Lattice& L, const Coef<C>& k, int wal
     d.g = L.g;
     d.v = vals_of(k);
     d.st = L.st;
+    d.wallx = L.wallx;
     d.wall0 = wall0;
     d.nstrips = L.nstrips;
     d.ntiles_y = ntiles;

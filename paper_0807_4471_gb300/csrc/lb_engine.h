@@ -14,9 +14,10 @@ namespace lbgb {
 struct Lattice {
     lb_params p;
     Geom g;
-    char* region;            // device region: stats | observe slots | buffer 0 | buffer 1
+    char* region;            // device region: stats | observe slots | wall columns | buffer 0 | buffer 1
     DevStats* st;
     double* slots;           // observe partial sums, 4 per tile
+    char* wallx;             // the step's wall-momentum pairs: [2][nx] (bottom, top), compute type
     char* fbuf[2];
     size_t fbytes;
     CUtensorMap tblock[2];   // step kernel: 8-row block loads of buffer b

@@ -107,6 +107,8 @@ struct alignas(128) LatDesc {
     LatVals<C> v;
     void* fbuf[2];
     DevStats* st;
+    void* wallx;           // [2][nx] compute-type pairs: x-momentum handed to the bottom
+                           // (then top) wall by the links leaving site x, this step
     int wall0;             // this lattice's wall items: wall_items[wall0 .. wall0 + 2 nstrips)
     int nstrips;           // ceil(nx / TX)
     int ntiles_y;          // tile rows of the launch's tile shape

@@ -2,25 +2,29 @@
 // pseudo-potential lattice Boltzmann step (Benzi, Chibbaro & Succi,
 // arXiv:0807.4471, Eqs. (1)-(2)).
 //
-// One launch of k_step advances every site of the lattice by one time step.
-// Layout in HBM: 9 direction planes, each a ghost-padded [ny + 6][pitch]
-// array of interleaved (A, B) pairs of the storage type, holding offsets
-// h_i = f_i - w_i rho_ref.  The buffer read by a step holds the
-// post-collision populations f*(t-1) of the previous step; streaming is a
-// pull, f_i(r, t) = f*_i(r - c_i, t - 1).
+// One launch of k_step advances every site of a set of lattices by one time
+// step.  Layout in HBM: 9 direction planes, each a ghost-padded
+// [ny + 6][pitch] array of interleaved (A, B) pairs of the storage type,
+// holding offsets h_i = f_i - w_i rho_ref.  The buffer read by a step holds
+// the post-collision populations f*(t-1) of the previous step; streaming is
+// a pull, f_i(r, t) = f*_i(r - c_i, t - 1).
 //
-// k_step is persistent: one CTA per SM walks the TX x TY tiles.  Per tile:
-//  1. TMA: one 3-D box load brings f* on the tile plus a 3-cell halo (both
-//     species, 9 planes) into shared memory; the next tile's box loads into
-//     the second buffer meanwhile.  The ghost columns/rows of the padded
-//     planes hold periodic copies, so a box never wraps.
-//  2. density and pseudo-potential deviations on the tile plus a 2-cell halo
-//     (halfway bounce-back at Couette walls; mirrored beyond a wall).
-//  3. one site per thread: moments, the force of Eq. (2) from the shared
-//     tiles (12 antisymmetric pairs of the 24-neighbour stencil, 4 pairs of
-//     the cross term), the forced BGK relaxation of Eq. (1) into a staging
-//     tile, written back by a TMA bulk tensor store (plus ghost copies).
-//  4. Couette: FP64 wall-momentum sums, per-CTA slots, last CTA samples.
+// k_step is persistent: one CTA per SM walks its work items (a lattice's
+// strip of TX x TY tiles, one after the other).  Per tile:
+//  1. TMA: 3-D box loads bring f* in 8-row blocks (both species, 9 planes,
+//     the strip plus its ghost columns) into a ring of shared-memory slots,
+//     several blocks ahead.  The ghost columns/rows of the padded planes
+//     hold periodic copies, so a box never wraps.
+//  2. density phase: density and pseudo-potential deviations on the tile
+//     plus a 2-row halo (halfway bounce-back at Couette walls; mirrored
+//     beyond a wall), and at tau = 1 the momenta of the tile's sites.
+//  3. site phase, one or two sites per thread: the force of Eq. (2) from the
+//     shared deviation window (row sums of the 24-neighbour stencil and of
+//     the cross term), the forced BGK relaxation of Eq. (1), the write-back
+//     (staging tile + TMA bulk tensor store, or direct stores) and the
+//     periodic ghost copies.
+//  4. Couette: the wall sites' momentum exchange, summed per strip in FP64
+//     after the tile loop; the last CTA takes the wall samples.
 // There is no dense contraction anywhere, so no tensor cores are used.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -221,21 +225,24 @@ __device__ __forceinline__ C2 dpsi_of(C2 d, const LatVals<C>& v) {
 
 // Momentum j = sum_i c_i f_i of both species from the offsets (sum_i w_i c_i
 // = 0, so the offsets carry all of j), in the compute scale.
-template <int P>
+// SCALED = false: left in the storage scale (the caller folds the scale,
+// a power of two, into a later factor).
+template <int P, bool SCALED = true>
 __device__ __forceinline__ void moments(const typename Prec<P>::C2 h[9], typename Prec<P>::C2& jx,
                                         typename Prec<P>::C2& jy) {
     typedef typename Prec<P>::C2 C2;
     const C2 d57 = psub(h[5], h[7]), d68 = psub(h[6], h[8]);
     jx = padd(psub(h[1], h[3]), psub(d57, d68));
     jy = padd(psub(h[2], h[4]), padd(d57, d68));
-    if constexpr (Prec<P>::SCALE_LOG2 != 0) {
+    if constexpr (SCALED && Prec<P>::SCALE_LOG2 != 0) {
         jx = pmul(jx, pset(inv_scale_of<P>()));
         jy = pmul(jy, pset(inv_scale_of<P>()));
     }
 }
 
 // Density and pseudo-potential deviations (rho - rho_ref, Psi - Psi(rho_ref))
-// of both species at one site; with J, also the site's momentum.
+// of both species at one site; with J, also the site's momentum, in the
+// storage scale.
 template <int P, int PS, bool J = false>
 __device__ __forceinline__ void cell_dev(const typename Prec<P>::T2* bm,
                                          const typename Prec<P>::T2* b0,
@@ -248,7 +255,7 @@ __device__ __forceinline__ void cell_dev(const typename Prec<P>::T2* bm,
     r = sum9(h);
     if constexpr (Prec<P>::SCALE_LOG2 != 0) r = pmul(r, pset(inv_scale_of<P>()));
     q = dpsi_of(r, v);
-    if constexpr (J) moments<P>(h, j[0], j[1]);
+    if constexpr (J) moments<P, false>(h, j[0], j[1]);
 }
 
 // Post-collision offsets of both species (Eq. (1), BGK toward the
@@ -463,6 +470,7 @@ struct SiteOut {
                            // the site updates of a thread free of branches:
                            // its global stores and non-finite flag are dropped
     int obs;               // ObsKind (observe kernel) or OBS_NONE
+    void* wallx;           // step: the lattice's wall-momentum pairs, [2][nx] compute type
     double* obs_out;
     int q0, q1;
 };
@@ -472,7 +480,8 @@ struct SiteOut {
 // write-back (OBS = false) or the observables (OBS = true).  Both species are
 // carried as (A, B) pairs throughout.  TAU1 (omega = 1 for both species,
 // OBS = false): the collision needs the populations only through j, which the
-// caller passes in jg = {jx, jy}; bm, b0 and bp are not read.
+// caller passes in jg = {jx, jy} (in the storage scale); bm, b0 and bp are
+// not read.
 template <int P, bool OBS, bool GEN, int PS, int SINK, bool TAU1 = false>
 __device__ __forceinline__ void site_update(
     const typename Prec<P>::T2* bm, const typename Prec<P>::T2* b0,
@@ -548,7 +557,9 @@ __device__ __forceinline__ void site_update(
     const C2 ro = TAU1 ? rho : pmul(rho, om), jxo = TAU1 ? jx : pmul(jx, om),
              jyo = TAU1 ? jy : pmul(jy, om);
     const C den = ro.x + ro.y;
-    const C inv3 = den != C(0) ? C(3) * recip(den) : C(0);
+    // 3 / den, times the storage scale's inverse where j is taken in the
+    // storage scale (TAU1; both factors exact powers of two apart)
+    const C inv3 = den != C(0) ? (TAU1 ? C(3) * inv_scale_of<P>() : C(3)) * recip(den) : C(0);
     const C2 vp = pair((jxo.x + jxo.y) * inv3, (jyo.x + jyo.y) * inv3);
     const bool source = GEN && k.source;
     C2 vx = pset(vp.x), vy = pset(vp.y);
@@ -613,7 +624,8 @@ __device__ __forceinline__ void site_update(
         // 2 (f*_a - f*_b) - 6 rho_w u_w (w_a + w_b) = 2 (f*_a - f*_b) - rho_w u_w / 3
         // with (a, b) = (8, 7) at the bottom wall and (5, 6) at the top
         // (c_ax = 1, c_bx = -1; w_a = w_b, so the offsets' difference is the
-        // populations').  One FP32 value per site and species, one FP64 add.
+        // populations').  One compute-type value per site and species, kept
+        // in the lattice's wall columns for the sums after the tile loop.
         const int down = (y == 0);
         const C uw = down ? -v.u_wall : v.u_wall;
         C2 sv[9];
@@ -622,8 +634,86 @@ __device__ __forceinline__ void site_update(
         const C2 rw2 = pfma(sum9(sv), pset(inv_scale_of<P>()), pset(v.rho_ref));
         const C2 dd = pmul(down ? psub(sv[8], sv[7]) : psub(sv[5], sv[6]), pset(inv_scale_of<P>()));
         const C2 m = psub(pmul(pset(C(2)), dd), pmul(rw2, pset(uw * (C(1) / C(3)))));
-        const double sum = (double)m.x + (double)m.y;
-        if (down) red[0] += sum; else red[1] += sum;
+        if (o.valid) reinterpret_cast<C2*>(o.wallx)[(down ? 0 : g.nx) + x] = m;
+    }
+}
+
+// Wall momentum of one CTA's items that hold a wall row, in FP64: the
+// wall-site values the site phase left in the lattice's wall columns, summed
+// over the item's strip in a fixed order (lane l takes columns l, l + 32,
+// ..., then the butterfly), one warp per item -- so the sums do not depend
+// on the partition or the tile shape.
+template <int P, int SPT>
+__device__ __forceinline__ void wall_sums(const BatchArgs<typename Prec<P>::C>& a, int it0, int it_end,
+                                       int tid) {
+    typedef Layout<P, SPT> L;
+    typedef typename L::C C;
+    typedef typename L::C2 C2;
+    const int lane = tid & 31, warp = tid >> 5;
+    int n = 0;
+    for (int it = it0; it < it_end; ++it) {
+        const int4 w = a.items[it];
+        const LatDesc<C>* d = &a.lat[w.x];
+        const bool bot = w.z == 0, top = w.w == d->ntiles_y;
+        if (d->g.periodic || !(bot || top)) continue;
+        if (n++ % (L::NT / 32) != warp) continue;
+        const int nx = d->g.nx;
+        const int xe = min(w.y * L::TX + L::TX, nx);
+        const C2* wx = reinterpret_cast<const C2*>(d->wallx);
+        double sb = 0.0, st = 0.0;
+        for (int x = w.y * L::TX + lane; x < xe; x += 32) {
+            if (bot) sb += (double)wx[x].x + (double)wx[x].y;
+            if (top) st += (double)wx[nx + x].x + (double)wx[nx + x].y;
+        }
+        sb = warp_sum(sb);
+        st = warp_sum(st);
+        if (lane == 0) {
+            a.slots[2 * it] = sb;
+            a.slots[2 * it + 1] = st;
+        }
+    }
+}
+
+// The last CTA of a step launch: advance every lattice's step counter and
+// buffer parity and take the Couette wall samples.  (Inlined: out of line,
+// measured on GB300, the sweeps ran 3-7 % slower.)
+template <int P, bool ALLPER, int NT>
+__device__ __forceinline__ void advance_lattices(const BatchArgs<typename Prec<P>::C>& a, int tid) {
+    typedef typename Prec<P>::C C;
+    // One warp per lattice.  The wall samples are summed over the strips in
+    // a fixed order -- lane l adds strips l, l + 32, ..., then a butterfly
+    // over the lanes -- so they do not depend on the partition; FP64 has a
+    // long latency on this GPU, so no serial chain runs over the strips.
+    {
+        const int lane = tid & 31;
+        for (int l = tid >> 5; l < a.nlat; l += NT / 32) {
+            const LatDesc<C>* d = &a.lat[l];
+            DevStats* st = d->st;
+            const long long t = st->t;
+            if (!ALLPER && !d->g.periodic) {
+                const int ns = d->nstrips;
+                const int* wi = a.wall_items + d->wall0;
+                const volatile double* vs = a.slots;
+                double sb = 0.0, stp = 0.0;
+                for (int i = lane; i < ns; i += 32) {
+                    sb += vs[2 * wi[i]];
+                    stp += vs[2 * wi[ns + i] + 1];
+                }
+                sb = warp_sum(sb);
+                stp = warp_sum(stp);
+                const long long every = d->stress_every > 0 ? d->stress_every : 1;
+                if (lane == 0 && t >= d->stress_t0 && ((t - d->stress_t0) % every) == 0) {
+                    st->sum_bot += sb * d->inv_nx;
+                    st->sum_top += stp * d->inv_nx;
+                    st->samples += 1;
+                }
+            }
+            if (lane == 0) {
+                st->t = t + 1;
+                st->cur ^= 1;
+                st->pull = 1;
+            }
+        }
     }
 }
 
@@ -724,7 +814,8 @@ __device__ __forceinline__ void block_sum4(double red[4], double (*s_red)[4]) {
 // 16-row tiles) the threads store their sites and ghost copies to global
 // memory themselves.  The last CTA to finish advances every lattice's step
 // counter and buffer parity and takes the Couette wall samples.
-// V: bit 0 = every lattice periodic (no wall code); bit 1 = general forcing.
+// V: bit 0 = every lattice periodic (no wall code); bit 1 = general forcing;
+// bit 2 = omega = 1 for both species (the site phase reads no populations).
 template <int P, int V, int SPT>
 __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
     k_step(const __grid_constant__ BatchArgs<typename Prec<P>::C> a) {
@@ -748,7 +839,6 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
     T2* stage = reinterpret_cast<T2*>(smem + L::STAGE_OFF);   // staging tile (STAGED)
     __shared__ __align__(8) uint64_t bars[L::NB];
     __shared__ int s_fail, s_last;
-    __shared__ double s_red[L::NT / 32][4];
     __shared__ uint64_t s_pol[2];   // L2 policies of the block loads and the tile stores
 
     const int tid = threadIdx.x;
@@ -771,8 +861,9 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
     // whose sites sit in the two rows carried over from the previous tile,
     // compute the last two rows -- the next tile's first sites, theirs again.
     // So every thread's sites were computed by the thread itself, in this
-    // tile or (first thread rows) in the previous one, and their momenta can
-    // stay in its registers (TAU1).
+    // tile or (first thread rows) in the previous one, and their momenta stay
+    // with it (TAU1): in registers, and for the first thread rows across the
+    // tile boundary in a small shared buffer of their own.
     constexpr int kCarry = 2 / SPT;   // thread rows whose sites are carried rows
     static_assert(2 % SPT == 0, "two carried rows per tile");
     const int t_m = (t_j + L::TYB - kCarry) % L::TYB;
@@ -782,9 +873,10 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
     // column (t_lx + 2) mod RX -- its own site column, and for the RX - TX
     // threads without a site the halo columns.
     const int t_w = (t_lx + 2) % L::RX;
-    // TAU1: momenta (jx, jy) of this thread's sites computed in the previous
-    // tile (used by the first thread rows) and in this one
-    C2 jprev[SPT][2];
+    // TAU1: momenta (jx, jy) of the first thread rows' new cells, kept for
+    // the next tile, whose first sites they are; jc: this thread's entries
+    __shared__ __align__(16) C2 s_jcarry[kCarry * L::RX * SPT * 2];
+    C2* const jc = s_jcarry + ((t_carry ? t_j : 0) * L::RX + t_lx) * (SPT * 2);
     auto slot = [&](int pos) { return reinterpret_cast<T2*>(smem + (pos % L::NB) * L::SLOT_BYTES); };
     const int it_end = a.cta_items[blockIdx.x + 1];
 
@@ -863,7 +955,6 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
         // the step counter advances only after every CTA of the launch is done
         const uint32_t key = hash32((uint32_t)*((volatile long long*)&d->st->t) * 0x9e3779b9u);
         T2* fout = reinterpret_cast<T2*>(d->fbuf[cur ^ 1]);
-        double wall[2] = {0.0, 0.0};
         // ring slot and phase parity of the tile's first block, kept as the
         // tiles advance
         int qm = c_pos % L::NB, qph = (c_pos / L::NB) & 1;
@@ -924,11 +1015,15 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
                         const int kk = k - L::TY;
                         if (kk >= 0) {
                             if (ty == ty_a) {
-                                C2 r, p;
+                                C2 r, p, jt[2];
                                 cell_dev<P, PS, TAU1>(brow(kk, bc), brow(kk + 1, bc), brow(kk + 2, bc),
-                                                      y0 - 2 + kk, per, pull, g, v, r, p, jprev[c]);
+                                                      y0 - 2 + kk, per, pull, g, v, r, p, jt);
                                 win_r[kk * L::RX + t_w] = r;
                                 win_p[kk * L::RX + t_w] = p;
+                                if (TAU1 && t_carry) {   // rows 2 and 3: this thread's sites
+                                    jc[2 * c] = jt[0];
+                                    jc[2 * c + 1] = jt[1];
+                                }
                             } else {
                                 win_r[kk * L::RX + t_w] = win_r[k * L::RX + t_w];
                                 win_p[kk * L::RX + t_w] = win_p[k * L::RX + t_w];
@@ -948,6 +1043,19 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
                                               per, pull, g, v, r, p, jn[c]);
                         win_r[k * L::RX + t_w] = r;
                         win_p[k * L::RX + t_w] = p;
+                    }
+                    // The first thread rows (whole warps) swap their new cells'
+                    // momenta, the next tile's, for their sites', kept from the
+                    // previous tile; jn then holds every thread's sites'.
+                    if (TAU1 && t_carry) {
+    #pragma unroll
+                        for (int c = 0; c < SPT; ++c) {
+                            const C2 px = jc[2 * c], py = jc[2 * c + 1];
+                            jc[2 * c] = jn[c][0];
+                            jc[2 * c + 1] = jn[c][1];
+                            jn[c][0] = px;
+                            jn[c][1] = py;
+                        }
                     }
                 }
                 // mirror the deviations about the halfway walls, in the tiles whose
@@ -993,6 +1101,7 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
                         if constexpr (sizeof(T2) == 4) srh = sr_hash(key, x, y, g.nx);
                         o.obs = OBS_NONE;
                         o.valid = 1;
+                        o.wallx = d->wallx;
                         if constexpr (!STAGED) {
                             o.plane = g.plane;
                             o.gdx = x < 3 ? g.nx : (x >= g.nx - 3 ? -g.nx : 0);
@@ -1017,33 +1126,19 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
                                         : ys < 3 ? (long long)g.ny * g.pitch
                                         : (ys >= g.ny - 3 ? -(long long)g.ny * g.pitch : 0);
                             }
-                            double wr[4] = {0.0, 0.0, 0.0, 0.0};
+                            double wr[4];   // (observables only)
                             if constexpr (TAU1) {
-                                C2 js[2];
-                                js[0] = t_carry ? jprev[s][0] : jn[s][0];
-                                js[1] = t_carry ? jprev[s][1] : jn[s][1];
                                 site_update<P, false, GEN, PS, STAGED ? SINK_STAGE : SINK_GLOBAL, true>(
                                     nullptr, nullptr, nullptr, fx[s], fy[s], qx[s], qy[s], dp[s], dr[s],
-                                    x, ys, per, pull, g, v, a.k, o, wr, bad, js);
+                                    x, ys, per, pull, g, v, a.k, o, wr, bad, jn[s]);
                             } else {
                                 site_update<P, false, GEN, PS, STAGED ? SINK_STAGE : SINK_GLOBAL>(
                                     brow(ly + s + 2, bc), brow(ly + s + 3, bc), brow(ly + s + 4, bc),
                                     fx[s], fy[s], qx[s], qy[s], dp[s], dr[s], x, ys, per, pull, g, v,
                                     a.k, o, wr, bad);
                             }
-                            if (!per && (ys == 0 || ys == g.ny - 1)) {   // FP64: wall rows only
-                                wall[0] += wr[0];
-                                wall[1] += wr[1];
-                            }
                         }
                         if constexpr (STAGED) fence_proxy_async();   // staging writes before the bulk store
-                    }
-                }
-                if constexpr (TAU1) {
-#pragma unroll
-                    for (int c = 0; c < SPT; ++c) {
-                        jprev[c][0] = jn[c][0];
-                        jprev[c][1] = jn[c][1];
                     }
                 }
                 return true;
@@ -1091,35 +1186,17 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
         }
         if (s_fail) break;
         c_pos += SPT * (ty_b - ty_a) + 1;
-        if (!per_lat && (ty_a == 0 || ty_b == d->ntiles_y)) {
-            // Wall momentum of an item holding a wall row (only these items'
-            // slots are read), in FP64.  FP64 issues at a small fraction of
-            // the FP32 rate and with a long latency, so only the warps that
-            // updated a wall site reduce, and warp 0 adds the warps' sums by
-            // a fixed tree (zero for the others).
-            const int lane = tid & 31, warp = tid >> 5;
-            const bool mine = __any_sync(0xffffffffu, wall[0] != 0.0 || wall[1] != 0.0);
-            if (mine) {
-                wall[0] = warp_sum(wall[0]);
-                wall[1] = warp_sum(wall[1]);
-            }
-            __syncthreads();   // the previous item's reads of s_red are done
-            if (lane == 0) {
-                s_red[warp][0] = mine ? wall[0] : 0.0;
-                s_red[warp][1] = mine ? wall[1] : 0.0;
-            }
-            __syncthreads();
-            if (warp == 0) {
-                double b = lane < L::NT / 32 ? s_red[lane][0] : 0.0;
-                double t = lane < L::NT / 32 ? s_red[lane][1] : 0.0;
-                b = warp_sum(b);
-                t = warp_sum(t);
-                if (lane == 0) {
-                    a.slots[2 * it] = b;
-                    a.slots[2 * it + 1] = t;
-                }
-            }
-        }
+    }
+    // Wall momentum of this CTA's items that hold a wall row, in FP64: the
+    // wall-site values the site phase left in the lattice's wall columns,
+    // summed over the item's strip in a fixed order (lane l takes columns
+    // l, l + 32, ..., then the butterfly), one warp per item -- so the sums
+    // do not depend on the partition or the tile shape.  Kept out of the
+    // tile loop: a per-item reduction there (barriers, FP64 shuffles) cost
+    // the generic variant 1-4 % even on periodic lattices, which skip it.
+    if constexpr (!ALLPER) {
+        __syncthreads();   // this CTA's wall-site values are written
+        if (!s_fail) wall_sums<P, SPT>(a, a.cta_items[blockIdx.x], it_end, tid);
     }
     if (STAGED && tid == kStoreThread) bulk_wait_all();
     if (s_fail && tid == 0) {
@@ -1142,41 +1219,7 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // One warp per lattice.  The wall samples are summed over the strips in
-    // a fixed order -- lane l adds strips l, l + 32, ..., then a butterfly
-    // over the lanes -- so they do not depend on the partition; FP64 has a
-    // long latency on this GPU, so no serial chain runs over the strips.
-    {
-        const int lane = tid & 31;
-        for (int l = tid >> 5; l < a.nlat; l += L::NT / 32) {
-            const LatDesc<C>* d = &a.lat[l];
-            DevStats* st = d->st;
-            const long long t = st->t;
-            if (!ALLPER && !d->g.periodic) {
-                const int ns = d->nstrips;
-                const int* wi = a.wall_items + d->wall0;
-                const volatile double* vs = a.slots;
-                double sb = 0.0, stp = 0.0;
-                for (int i = lane; i < ns; i += 32) {
-                    sb += vs[2 * wi[i]];
-                    stp += vs[2 * wi[ns + i] + 1];
-                }
-                sb = warp_sum(sb);
-                stp = warp_sum(stp);
-                const long long every = d->stress_every > 0 ? d->stress_every : 1;
-                if (lane == 0 && t >= d->stress_t0 && ((t - d->stress_t0) % every) == 0) {
-                    st->sum_bot += sb * d->inv_nx;
-                    st->sum_top += stp * d->inv_nx;
-                    st->samples += 1;
-                }
-            }
-            if (lane == 0) {
-                st->t = t + 1;
-                st->cur ^= 1;
-                st->pull = 1;
-            }
-        }
-    }
+    advance_lattices<P, ALLPER, L::NT>(a, tid);
     __threadfence();
     if (tid == 0) *a.ticket = 0u;
 }
