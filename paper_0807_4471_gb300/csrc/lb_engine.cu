@@ -686,8 +686,19 @@ lb_status lattice_read_stats(Lattice& L, DevStats* out, cudaStream_t s) {
     return LB_OK;
 }
 
+// The first step >= t at which the wall momentum is sampled:
+// stress_t0 + k stress_every, k >= 0.
+static long long first_sample(const lb_params& p, long long t) {
+    if (t <= p.stress_t0) return p.stress_t0;
+    const long long every = p.stress_every > 0 ? p.stress_every : 1;
+    return p.stress_t0 + (t - p.stress_t0 + every - 1) / every * every;
+}
+
 static lb_status lattice_reset(Lattice& L, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(L.st, 0, sizeof(DevStats), s);   // t = 0, cur = 0, pull = 0
+    L.next_sample = first_sample(L.p, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&L.st->next_sample, &L.next_sample, sizeof(long long), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_status(e);
     L.t = 0;
     L.cur = 0;
@@ -753,6 +764,10 @@ lb_status lattice_load_populations(Lattice& L, const double* f, long long t, int
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&L.st->t, &t, sizeof(long long), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&L.st->pull, &pulled, sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the reset's copy has read next_sample
+    L.next_sample = first_sample(L.p, t);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&L.st->next_sample, &L.next_sample, sizeof(long long), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_status(e);
     L.t = t;

@@ -30,6 +30,8 @@ struct Lattice {
     bool inited;
     long long t;             // host mirror of the step count
     unsigned int err_latched;
+    long long next_sample;   // source of the device's DevStats::next_sample (lives with
+                             // the lattice, so the asynchronous copy needs no wait)
 };
 
 // One launch of the persistent step kernel over a set of lattices.

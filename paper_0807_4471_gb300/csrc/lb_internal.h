@@ -23,7 +23,10 @@ struct DevStats {
     double totals[4];       // last observe pass: mass_A, mass_B, mom_x, mom_y
     int cur;                // buffer holding the current state (0 or 1)
     int pull;               // 1: it holds post-collision f*(t-1); 0: f(t) in place
-    double pad_[6];
+    long long next_sample;  // the next step whose wall momentum is sampled
+                            // (stress_t0 + k stress_every >= t; set by the host
+                            // with t, advanced by the kernel)
+    double pad_[5];
 };
 static_assert(sizeof(DevStats) == 128, "DevStats is one 128-byte line");
 

@@ -701,11 +701,14 @@ __device__ __forceinline__ void advance_lattices(const BatchArgs<typename Prec<P
                 }
                 sb = warp_sum(sb);
                 stp = warp_sum(stp);
-                const long long every = d->stress_every > 0 ? d->stress_every : 1;
-                if (lane == 0 && t >= d->stress_t0 && ((t - d->stress_t0) % every) == 0) {
+                // sampled steps: stress_t0 + k stress_every, tracked by
+                // next_sample (no 64-bit remainder: it would compile to a
+                // call, which burdens the whole kernel's register allocation)
+                if (lane == 0 && t == st->next_sample) {
                     st->sum_bot += sb * d->inv_nx;
                     st->sum_top += stp * d->inv_nx;
                     st->samples += 1;
+                    st->next_sample = t + (d->stress_every > 0 ? d->stress_every : 1);
                 }
             }
             if (lane == 0) {

@@ -402,6 +402,28 @@ def test_checkpoint_restore(lb, prec, boundary):
     h.close()
 
 
+def test_restore_keeps_the_stress_sampling_schedule(lb):
+    """Wall samples are taken at stress_t0 + k stress_every.  A lattice
+    restored at step 29 (stress_t0 = 10, every 4) samples at 30, 34, ...,
+    exactly like a run whose window starts at 30: same count, bitwise the
+    same sums (FP32 storage restores bitwise)."""
+    m = model(96, 40, boundary=1, u_wall=0.02, init_shear=1, stress_t0=10, stress_every=4)
+    g = lb.Lattice(gpu_params(lb, m, "fp32")).init_seeded(7)
+    g.step(29)
+    state, t, pulled = g.checkpoint()
+    h = lb.Lattice(gpu_params(lb, m, "fp32")).resume(state, t, pulled)
+    h.step(41)
+    c = lb.Lattice(gpu_params(lb, model(96, 40, boundary=1, u_wall=0.02, init_shear=1, stress_t0=30,
+                                        stress_every=4), "fp32")).init_seeded(7)
+    c.step(70)
+    sh, sc = h.stress(), c.stress()
+    assert sh["samples"] == sc["samples"] == 10
+    for key in ("sigma_bot", "sigma_top"):
+        assert sh[key] == sc[key], key
+    for x in (g, h, c):
+        x.close()
+
+
 def test_init_populations_from_oracle(lb, O):
     """Start from populations given on the host (here the oracle's state at
     step 20) and continue: matches the oracle's continuation (FP64)."""
