@@ -21,6 +21,13 @@ int kernel_elem_bytes(int p) { LB_SWITCH(p, return (int)sizeof(typename Layout<P
 int kernel_smem_obs_bytes(int p) { LB_SWITCH(p, return Layout<P>::SMEM_OBS) return 0; }
 int kernel_block_rows(int p) { LB_SWITCH(p, return Layout<P>::TYB) return 0; }
 int kernel_scale_log2(int p) { LB_SWITCH(p, return Prec<P>::SCALE_LOG2) return 0; }
+template <int P>
+static int staged_of(int spt) {
+    if constexpr (Prec<P>::NB2 > 0)
+        if (spt == 2) return Layout<P, 2>::STAGED ? 1 : 0;
+    return Layout<P, 1>::STAGED ? 1 : 0;
+}
+int kernel_staged(int p, int spt) { LB_SWITCH(p, return staged_of<P>(spt)) return 1; }
 
 cudaError_t launch_step(int precision, const void* args, int variant, int spt, dim3 grid,
                         cudaStream_t s) {

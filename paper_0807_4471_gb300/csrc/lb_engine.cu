@@ -5,6 +5,7 @@
 // step of the model runs in the kernels of lb_kernels.cu.
 #include "lb_engine.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -363,23 +364,28 @@ void partition(Lattice* const* lats, int nlat, int seg, int spt, int sms, std::v
         nty[(size_t)l] = tiles_y(*lats[l], spt);
         tiles += (long long)lats[l]->nstrips * nty[(size_t)l];
     }
-    // Tile costs measured on GB300, relative to a full interior tile: tiles
-    // that write periodic ghost copies, and Couette tiles holding a wall row
-    // (mirror, bounce-back, wall momentum), 1.26; ragged tiles 1.04; and the
-    // first tile of an item one tile more (its block ring fills and it
-    // computes four more deviation rows).
+    // Tile costs relative to a full interior tile, fitted on GB300 to the
+    // per-CTA times of single steps (5 x 512^2 sweeps, periodic and Couette,
+    // FP32 and FP16, 16-row tiles): tiles writing periodic ghost columns
+    // +0.21; ghost rows +0.25 where they leave through the staging tile, +0.02
+    // where the threads store them directly; Couette tiles holding a wall row
+    // (mirror, bounce-back, wall momentum) 1.38; ragged tiles 1.07; and an
+    // item's start (its block ring fills, it computes four more deviation
+    // rows) 0.8 of a tile.
     auto cost = [&](int l, int sx, int ty) {
         const Lattice& L = *lats[l];
         const int tx = kernel_tile_x(L.p.precision), tyy = kernel_tile_y(L.p.precision) * spt;
         const int x0 = sx * tx, y0 = ty * tyy;
         const bool full = x0 + tx <= L.p.nx && y0 + tyy <= L.p.ny;
-        if (!full) return 1.04;
+        if (!full) return 1.07;
         const bool per = L.g.periodic != 0;
-        const bool edge = x0 < 3 || x0 + tx > L.p.nx - 3 || (per && (y0 < 3 || y0 + tyy > L.p.ny - 3)) ||
-                          (!per && (y0 == 0 || y0 + tyy >= L.p.ny));
-        return edge ? 1.26 : 1.0;
+        if (!per && (y0 == 0 || y0 + tyy >= L.p.ny)) return 1.38;
+        double c = 1.0;
+        if (x0 < 3 || x0 + tx > L.p.nx - 3) c += 0.21;
+        if (per && (y0 < 3 || y0 + tyy > L.p.ny - 3)) c += kernel_staged(L.p.precision, spt) ? 0.25 : 0.02;
+        return c;
     };
-    const double kItemStart = 1.0;
+    const double kItemStart = 0.8;
     if (seg > 0) {
         // Segments in band order (all strips of a segment row, row after row),
         // each given to the CTA with the least work so far (the lowest index
@@ -412,38 +418,64 @@ void partition(Lattice* const* lats, int nlat, int seg, int spt, int sms, std::v
         *grid = G;
         return;
     }
-    const int G = (int)std::min<long long>(tiles, sms);
-    // The runs cut the tile sequence at equal cumulative cost, counting an
-    // item start wherever a run begins or crosses a strip.
-    double total = 0.0;
+    // Contiguous runs over the tiles in order (lattice, strip, tile row); a
+    // run pays an item start where it begins and where it crosses into the
+    // next strip.  The runs minimise the largest run cost: the smallest bound
+    // B for which runs filled greedily (a run takes the next tile while its
+    // cost stays within B) number at most sms, found by bisection -- at most
+    // one tile above the mean, where cutting at equal cumulative cost lets
+    // some runs overshoot by a whole tile.
+    std::vector<double> tc;
+    std::vector<char> sbeg;   // tile begins a strip
+    tc.reserve((size_t)tiles);
+    sbeg.reserve((size_t)tiles);
+    double sum = 0.0, cmax = 0.0;
     for (int l = 0; l < nlat; ++l)
-        for (int sx = 0; sx < lats[l]->nstrips; ++sx) {
-            total += kItemStart;
-            for (int ty = 0; ty < nty[(size_t)l]; ++ty) total += cost(l, sx, ty);
+        for (int sx = 0; sx < lats[l]->nstrips; ++sx)
+            for (int ty = 0; ty < nty[(size_t)l]; ++ty) {
+                tc.push_back(cost(l, sx, ty));
+                sbeg.push_back(ty == 0 ? 1 : 0);
+                sum += tc.back() + (ty == 0 ? kItemStart : 0.0);
+                cmax = std::max(cmax, tc.back());
+            }
+    // runs needed under bound B; with starts, the first tile of each run
+    auto runs_for = [&](double B, std::vector<long long>* starts) -> long long {
+        long long n = 0;
+        double acc = 0.0;
+        for (long long k = 0; k < tiles; ++k) {
+            const double add = tc[(size_t)k] + (sbeg[(size_t)k] ? kItemStart : 0.0);
+            if (n > 0 && acc + add <= B) {
+                acc += add;
+            } else {
+                ++n;
+                if (starts) starts->push_back(k);
+                acc = tc[(size_t)k] + kItemStart;
+            }
         }
-    total += kItemStart * G;   // roughly one extra item start per run
-    long long pos = 0;          // tiles assigned so far
+        return n;
+    };
+    double lo = cmax + kItemStart, hi = sum + kItemStart * (double)sms;
+    if (runs_for(lo, nullptr) > sms)
+        for (int it = 0; it < 60 && hi - lo > 1e-6 * hi; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (runs_for(mid, nullptr) <= sms) hi = mid; else lo = mid;
+        }
+    else
+        hi = lo;
+    std::vector<long long> starts;
+    runs_for(hi, &starts);
+    const int G = (int)starts.size();
+    starts.push_back(tiles);
+    // tile k -> (lattice, strip, tile row), walking the same order
     int l = 0, sx = 0, ty = 0;
-    double acc = 0.0;           // cumulative cost of the assigned tiles and item starts
     for (int b = 0; b < G; ++b) {
         cta.push_back((int)items.size());
-        const double target = total * (b + 1) / G;
-        // at least one tile per run, and leave one tile for each later run
-        const long long max_end = tiles - (G - 1 - b);
-        const bool last = b == G - 1;
-        bool first = true;
-        while (pos < max_end && (first || acc < target || last)) {
-            // an item of at least one tile, then as many as the run's cost allows
+        long long k = starts[(size_t)b];
+        while (k < starts[(size_t)b + 1]) {
             const int nt = nty[(size_t)l];
-            int take = 0;
-            acc += kItemStart;
-            do {
-                acc += cost(l, sx, ty + take);
-                ++take;
-            } while (ty + take < nt && pos + take < max_end && (acc < target || last));
-            first = false;
+            const int take = (int)std::min<long long>(nt - ty, starts[(size_t)b + 1] - k);
             items.push_back({l, sx, ty, ty + take});
-            pos += take;
+            k += take;
             ty += take;
             if (ty == nt) {
                 ty = 0;

@@ -168,6 +168,9 @@ int kernel_elem_bytes(int precision);
 int kernel_smem_obs_bytes(int precision);
 int kernel_block_rows(int precision);
 int kernel_scale_log2(int precision);
+// 1 if the step kernel with spt sites per thread leaves through a staging
+// tile (its periodic ghost copies are then separate stores after the tile)
+int kernel_staged(int precision, int spt);
 
 // Step: the persistent multi-lattice kernel (args: BatchArgs<C>), variant
 // bit 0 = every lattice periodic, bit 1 = general forcing, bit 2 = 1 - omega

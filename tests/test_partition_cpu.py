@@ -24,16 +24,25 @@ def lattices(lb, dims, prec="fp32"):
             for nx, ny, b in dims]
 
 
-def tile_cost(nx, ny, periodic, tx, sx, ty):
-    """The cost model the library documents: a ragged tile 1.04, a tile that
-    writes periodic ghost copies or holds a Couette wall row 1.26, an
-    interior tile 1."""
-    x0, y0 = sx * tx, ty * TY
-    if not (x0 + tx <= nx and y0 + TY <= ny):
-        return 1.04
-    edge = (x0 < 3 or x0 + tx > nx - 3 or (periodic and (y0 < 3 or y0 + TY > ny - 3))
-            or (not periodic and (y0 == 0 or y0 + TY >= ny)))
-    return 1.26 if edge else 1.0
+ITEM = 0.8   # an item's start, in tiles
+
+
+def tile_cost(nx, ny, periodic, tx, sx, ty, rows=TY, staged=True):
+    """The cost model the library documents: an interior tile 1; a ragged
+    tile 1.07; a Couette tile holding a wall row 1.38; +0.21 for writing
+    periodic ghost columns and +0.25 for ghost rows (+0.02 where the kernel
+    stores them directly, FP32 with 16-row tiles)."""
+    x0, y0 = sx * tx, ty * rows
+    if not (x0 + tx <= nx and y0 + rows <= ny):
+        return 1.07
+    if not periodic and (y0 == 0 or y0 + rows >= ny):
+        return 1.38
+    c = 1.0
+    if x0 < 3 or x0 + tx > nx - 3:
+        c += 0.21
+    if periodic and (y0 < 3 or y0 + rows > ny - 3):
+        c += 0.25 if staged else 0.02
+    return c
 
 
 def check_cover(items, cta, dims, tx, sms, ty_rows=TY):
@@ -94,7 +103,7 @@ def test_segments_balanced_by_cost(lb, dims, seg):
     def cost(it):
         l, sx, a, b = it
         nx, ny, bnd = dims[l]
-        return 1.0 + sum(tile_cost(nx, ny, bnd == 0, tx, sx, ty) for ty in range(a, b))
+        return ITEM + sum(tile_cost(nx, ny, bnd == 0, tx, sx, ty) for ty in range(a, b))
 
     loads = [sum(cost(items[k]) for k in range(cta[c], cta[c + 1])) for c in range(len(cta) - 1)]
     wmax = max(cost(it) for it in items)
@@ -110,29 +119,49 @@ def test_segments_balanced_by_cost(lb, dims, seg):
 
 
 @pytest.mark.parametrize("dims", CASES)
-def test_contiguous_runs(lb, dims):
+@pytest.mark.parametrize("rows,sms", [(8, 152), (16, 152), (16, 7)])
+def test_contiguous_runs(lb, dims, rows, sms):
     """seg = -1: the CTAs' items, concatenated, walk the tiles in order
-    (lattice, strip, tile row) and each CTA's run is one stretch of it; runs
-    are balanced by cost to within an item start and a tile or two (the
-    last run takes what is left, which may be less)."""
-    items, cta, _ = lb.lb_plan_partition(lattices(lb, dims), -1, 152)
+    (lattice, strip, tile row), each CTA's run one stretch of it, an item
+    per strip it touches; and the largest run cost is the least any split
+    into at most sms contiguous runs achieves: packing the runs greedily
+    under any smaller bound takes more than sms runs."""
+    items, cta, _ = lb.lb_plan_partition(lattices(lb, dims), -1, sms, tile_rows=rows)
     tx = TX["fp32"]
+    staged = rows == 8          # FP32 with 16-row tiles stores directly
     order = [(l, sx, ty) for l, (nx, ny, _) in enumerate(dims)
-             for sx in range(-(-nx // tx)) for ty in range(-(-ny // TY))]
+             for sx in range(-(-nx // tx)) for ty in range(-(-ny // rows))]
     walk = [(l, sx, ty) for l, sx, a, b in items for ty in range(a, b)]
     assert walk == order
     G = len(cta) - 1
+    assert 1 <= G <= sms
     loads = []
     for c in range(G):
         w = 0.0
         for l, sx, a, b in items[cta[c]:cta[c + 1]]:
             nx, ny, bnd = dims[l]
-            w += 1.0 + sum(tile_cost(nx, ny, bnd == 0, tx, sx, ty) for ty in range(a, b))
+            w += ITEM + sum(tile_cost(nx, ny, bnd == 0, tx, sx, ty, rows, staged) for ty in range(a, b))
         loads.append(w)
+    # tile costs in order, with an item start where a strip begins
+    seq = [(tile_cost(dims[l][0], dims[l][1], dims[l][2] == 0, tx, sx, ty, rows, staged), ty == 0)
+           for l, sx, ty in order]
+
+    def greedy_runs(bound):
+        n, acc = 0, 0.0
+        for c, first in seq:
+            add = c + (ITEM if first else 0.0)
+            if n and acc + add <= bound:
+                acc += add
+            else:
+                n, acc = n + 1, c + ITEM
+        return n
+
+    B = max(loads)
+    assert greedy_runs(B * (1 + 1e-9)) <= sms
+    if B > max(c for c, _ in seq) + ITEM + 1e-9:   # not a single tile's bound
+        assert greedy_runs(B * (1 - 1e-5)) > sms
     mean = sum(loads) / G
-    if len(order) >= 4 * G:       # enough tiles for the runs to be balanced
-        assert max(loads) <= mean + 3.6
-        assert min(loads[:-1]) >= mean - 3.6
+    assert B <= mean + max(c for c, _ in seq) + ITEM + 1e-9
 
 
 def test_default_rule(lb):
