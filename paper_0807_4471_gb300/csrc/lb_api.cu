@@ -42,7 +42,7 @@ HandleLayout handle_layout(const lb_params* p) {
     H.desc = off;
     off = align_up(off + sizeof(LatDesc<double>), kAlign);
     H.slots = off;
-    // wall slots and item tables (items <= tiles; up to 1024 CTAs)
+    // item tables (items <= tiles + strips; up to 1024 CTAs)
     off = align_up(off + sizeof(double) * launch_area_doubles(ntiles, nstrips, 1024), kAlign);
     H.total = off;
     return H;

@@ -103,7 +103,7 @@ static Geom make_geom(const lb_params* p) {
 // Device region of one lattice: stats, observe slots, wall columns, two
 // buffers.
 struct Region {
-    size_t stats, slots, wallx, f0, f1, total, fbytes;
+    size_t stats, slots, wallx, wsum, f0, f1, total, fbytes;
 };
 static Region region_layout(const lb_params* p) {
     Geom g = make_geom(p);
@@ -119,6 +119,9 @@ static Region region_layout(const lb_params* p) {
     // row), in the compute precision (at most two doubles)
     r.wallx = off;
     off = align_up(off + (size_t)2 * (size_t)p->nx * 2 * sizeof(double), kAlign);
+    // their sums per strip (at most nx strips), bottom then top
+    r.wsum = off;
+    off = align_up(off + (size_t)2 * (size_t)p->nx * sizeof(double), kAlign);
     r.fbytes = align_up((size_t)18 * (size_t)g.plane * (size_t)kernel_elem_bytes(p->precision), kAlign);
     r.f0 = off;
     off += r.fbytes;
@@ -247,6 +250,7 @@ lb_status lattice_setup(Lattice& L, const lb_params* p, char* region) {
     L.st = reinterpret_cast<DevStats*>(region + r.stats);
     L.slots = reinterpret_cast<double*>(region + r.slots);
     L.wallx = region + r.wallx;
+    L.wsum = reinterpret_cast<double*>(region + r.wsum);
     L.fbuf[0] = region + r.f0;
     L.fbuf[1] = region + r.f1;
     L.fbytes = r.fbytes;
@@ -319,7 +323,7 @@ int tiles_y(const Lattice& L, int spt) {
 }
 
 template <typename C>
-static void fill_desc(LatDesc<C>& d, const Lattice& L, const Coef<C>& k, int wall0, int ntiles) {
+static void fill_desc(LatDesc<C>& d, const Lattice& L, const Coef<C>& k, int ntiles) {
     memset(&d, 0, sizeof(d));
     for (int b = 0; b < 2; ++b) {
         d.tin[b] = L.tblock[b];
@@ -330,7 +334,7 @@ static void fill_desc(LatDesc<C>& d, const Lattice& L, const Coef<C>& k, int wal
     d.v = vals_of(k);
     d.st = L.st;
     d.wallx = L.wallx;
-    d.wall0 = wall0;
+    d.wsum = L.wsum;
     d.nstrips = L.nstrips;
     d.ntiles_y = ntiles;
     d.stress_every = L.p.stress_every;
@@ -339,8 +343,8 @@ static void fill_desc(LatDesc<C>& d, const Lattice& L, const Coef<C>& k, int wal
 }
 
 size_t launch_area_doubles(size_t tiles, size_t strips, int sms) {
-    // wall slots (2 per item) | items (int4) | CTA offsets | wall item lists
-    return 2 * tiles + 2 * tiles + ((size_t)sms + 2) / 2 + strips + 8;
+    // items (int4, at most one per tile and strip) | CTA offsets
+    return 2 * (tiles + strips) + ((size_t)sms + 2) / 2 + 8;
 }
 
 namespace {
@@ -577,40 +581,26 @@ lb_status launch_build(Launch& Ln, Lattice* const* lats, int nlat, void* descs, 
     int grid = 0;
     partition(lats, nlat, seg, spt, sms, items, cta, &grid);
     const int nitems = (int)items.size();
-    // wall item lists: per lattice, the bottom items by strip, then the top ones
-    std::vector<int> wall((size_t)(2 * strips), -1), wall0((size_t)nlat);
-    for (int l = 0, off = 0; l < nlat; ++l) {
-        wall0[(size_t)l] = off;
-        off += 2 * ns[(size_t)l];
-    }
-    for (int k = 0; k < nitems; ++k) {
-        const Item& w = items[(size_t)k];
-        if (w.ty_a == 0) wall[(size_t)(wall0[(size_t)w.lat] + w.strip)] = k;
-        if (w.ty_b == nt[(size_t)w.lat]) wall[(size_t)(wall0[(size_t)w.lat] + ns[(size_t)w.lat] + w.strip)] = k;
-    }
     const size_t dsz = prec == LB_FP64 ? sizeof(LatDesc<double>) : sizeof(LatDesc<float>);
     char* hs = reinterpret_cast<char*>(host_scratch);
     for (int l = 0; l < nlat; ++l) {
         lats[l]->seg = seg;
         if (prec == LB_FP64)
             fill_desc(*reinterpret_cast<LatDesc<double>*>(hs + l * dsz), *lats[l], lats[l]->kd,
-                      wall0[(size_t)l], nt[(size_t)l]);
+                      nt[(size_t)l]);
         else
             fill_desc(*reinterpret_cast<LatDesc<float>*>(hs + l * dsz), *lats[l], lats[l]->kf,
-                      wall0[(size_t)l], nt[(size_t)l]);
+                      nt[(size_t)l]);
     }
-    // device tables after the wall slots: items (16-byte aligned), CTA offsets, wall lists
-    int4* d_items = reinterpret_cast<int4*>(slots + 2 * (size_t)nitems);
+    // device tables: items (16-byte aligned), CTA offsets
+    int4* d_items = reinterpret_cast<int4*>(slots);
     int* d_cta = reinterpret_cast<int*>(d_items + nitems);
-    int* d_wall = d_cta + (grid + 1);
     static_assert(sizeof(Item) == sizeof(int4), "item layout");
     cudaError_t e = cudaMemcpyAsync(descs, hs, dsz * nlat, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * (size_t)nitems, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_cta, cta.data(), sizeof(int) * cta.size(), cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d_wall, wall.data(), sizeof(int) * wall.size(), cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);   // host buffers are reused
     if (e != cudaSuccess) return cuda_status(e);
     Ln.precision = prec;
@@ -640,8 +630,6 @@ lb_status launch_build(Launch& Ln, Lattice* const* lats, int nlat, void* descs, 
         a.nitems = nitems;
         a.items = d_items;
         a.cta_items = d_cta;
-        a.wall_items = d_wall;
-        a.slots = slots;
         a.ticket = ticket;
         a.l2_resident = l2_resident;
         a.early_release = early_release;
@@ -653,8 +641,6 @@ lb_status launch_build(Launch& Ln, Lattice* const* lats, int nlat, void* descs, 
         a.nitems = nitems;
         a.items = d_items;
         a.cta_items = d_cta;
-        a.wall_items = d_wall;
-        a.slots = slots;
         a.ticket = ticket;
         a.l2_resident = l2_resident;
         a.early_release = early_release;

@@ -14,10 +14,12 @@ namespace lbgb {
 struct Lattice {
     lb_params p;
     Geom g;
-    char* region;            // device region: stats | observe slots | wall columns | buffer 0 | buffer 1
+    char* region;            // device region: stats | observe slots | wall columns | wall sums |
+                             // buffer 0 | buffer 1
     DevStats* st;
     double* slots;           // observe partial sums, 4 per tile
     char* wallx;             // the step's wall-momentum pairs: [2][nx] (bottom, top), compute type
+    double* wsum;            // their per-strip sums: [2][nstrips]
     char* fbuf[2];
     size_t fbytes;
     CUtensorMap tblock[2];   // step kernel: 8-row block loads of buffer b
@@ -74,8 +76,8 @@ int tiles_y(const Lattice& L, int spt);
 // and the coefficients of lats[0] (couplings, tau, forcing).  seg > 0 forces
 // the segment length; seg = 0 takes choose_seg's; seg < 0 cuts the tiles
 // into one contiguous run per CTA.  `slots` holds launch_area_doubles(tiles,
-// strips, sms) doubles for the lattices' total tiles and strips: the per-item
-// wall slots and the item tables.
+// strips, sms) doubles for the lattices' total tiles and strips: the item
+// tables.
 // spt: sites per thread of the launch's kernel (1 or 2, see max_spt).
 lb_status launch_build(Launch& Ln, Lattice* const* lats, int nlat, void* descs, double* slots,
                        unsigned int* ticket, int sms, cudaStream_t stream, void* host_scratch,

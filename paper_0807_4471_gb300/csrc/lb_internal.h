@@ -112,7 +112,7 @@ struct alignas(128) LatDesc {
     DevStats* st;
     void* wallx;           // [2][nx] compute-type pairs: x-momentum handed to the bottom
                            // (then top) wall by the links leaving site x, this step
-    int wall0;             // this lattice's wall items: wall_items[wall0 .. wall0 + 2 nstrips)
+    double* wsum;          // [2][nstrips]: those summed per strip (bottom, then top)
     int nstrips;           // ceil(nx / TX)
     int ntiles_y;          // tile rows of the launch's tile shape
     int stress_every;
@@ -131,10 +131,6 @@ struct BatchArgs {
     // CTA: CTA b takes items cta_items[b] .. cta_items[b + 1] - 1 in order.
     const int4* items;
     const int* cta_items;
-    // Per lattice, the items holding its bottom wall row (strip order), then
-    // those holding its top wall row: the wall sums are taken in this order.
-    const int* wall_items;
-    double* slots;              // [nitems][2] wall-momentum partial sums
     unsigned int* ticket;       // CTA arrival counter of the launch (zero between launches)
     int l2_resident;            // one buffer of all lattices fits in L2: cache-policy hints
     int early_release;          // kernel variant bit 2 only: a tile's ring slots are refilled

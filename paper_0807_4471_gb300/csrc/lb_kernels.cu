@@ -116,6 +116,15 @@ __device__ __forceinline__ void griddep_launch_dependents() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Arrival at a launch's CTA counter: the old count, with release semantics
+// for this CTA's writes (made ordered before by a CTA barrier) and acquire
+// semantics for those of the CTAs that arrived before, at GPU scope.
+__device__ __forceinline__ unsigned int ticket_arrive(unsigned int* ticket) {
+    unsigned int old;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(ticket) : "memory");
+    return old;
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -668,55 +677,59 @@ __device__ __forceinline__ void wall_sums(const BatchArgs<typename Prec<P>::C>& 
         sb = warp_sum(sb);
         st = warp_sum(st);
         if (lane == 0) {
-            a.slots[2 * it] = sb;
-            a.slots[2 * it + 1] = st;
+            if (bot) d->wsum[w.y] = sb;
+            if (top) d->wsum[d->nstrips + w.y] = st;
         }
     }
 }
 
-// The last CTA of a step launch: advance every lattice's step counter and
-// buffer parity and take the Couette wall samples.  (Inlined: out of line,
-// measured on GB300, the sweeps ran 3-7 % slower.)
+// The last CTA of a step launch: the Couette wall samples, one warp per
+// lattice, then every lattice's step counter and buffer parity, one thread
+// per lattice.  t0, cur0: the step counter and buffer of lattice tid,
+// loaded by every CTA before its arrival (they change only between
+// launches), so the counters take no load on the launch's tail.
 template <int P, bool ALLPER, int NT>
-__device__ __forceinline__ void advance_lattices(const BatchArgs<typename Prec<P>::C>& a, int tid) {
+__device__ __forceinline__ void advance_lattices(const BatchArgs<typename Prec<P>::C>& a, int tid,
+                                                 long long t0, int cur0) {
     typedef typename Prec<P>::C C;
-    // One warp per lattice.  The wall samples are summed over the strips in
-    // a fixed order -- lane l adds strips l, l + 32, ..., then a butterfly
-    // over the lanes -- so they do not depend on the partition; FP64 has a
-    // long latency on this GPU, so no serial chain runs over the strips.
-    {
+    if constexpr (!ALLPER) {
+        // Strip sums in a fixed order -- lane l adds strips l, l + 32, ...,
+        // then a butterfly over the lanes -- so they do not depend on the
+        // partition; FP64 has a long latency on this GPU, so no serial chain
+        // runs over the strips.  Sampled steps: stress_t0 + k stress_every,
+        // tracked by next_sample (no 64-bit remainder: it would compile to a
+        // call, which burdens the whole kernel's register allocation).
         const int lane = tid & 31;
         for (int l = tid >> 5; l < a.nlat; l += NT / 32) {
             const LatDesc<C>* d = &a.lat[l];
+            if (d->g.periodic) continue;
             DevStats* st = d->st;
-            const long long t = st->t;
-            if (!ALLPER && !d->g.periodic) {
-                const int ns = d->nstrips;
-                const int* wi = a.wall_items + d->wall0;
-                const volatile double* vs = a.slots;
-                double sb = 0.0, stp = 0.0;
-                for (int i = lane; i < ns; i += 32) {
-                    sb += vs[2 * wi[i]];
-                    stp += vs[2 * wi[ns + i] + 1];
-                }
-                sb = warp_sum(sb);
-                stp = warp_sum(stp);
-                // sampled steps: stress_t0 + k stress_every, tracked by
-                // next_sample (no 64-bit remainder: it would compile to a
-                // call, which burdens the whole kernel's register allocation)
-                if (lane == 0 && t == st->next_sample) {
-                    st->sum_bot += sb * d->inv_nx;
-                    st->sum_top += stp * d->inv_nx;
-                    st->samples += 1;
-                    st->next_sample = t + (d->stress_every > 0 ? d->stress_every : 1);
-                }
+            const int ns = d->nstrips;
+            const volatile double* ws = d->wsum;
+            double sb = 0.0, stp = 0.0;
+            for (int i = lane; i < ns; i += 32) {
+                sb += ws[i];
+                stp += ws[ns + i];
             }
-            if (lane == 0) {
-                st->t = t + 1;
-                st->cur ^= 1;
-                st->pull = 1;
+            sb = warp_sum(sb);
+            stp = warp_sum(stp);
+            const long long t = st->t;
+            if (lane == 0 && t == st->next_sample) {
+                st->sum_bot += sb * d->inv_nx;
+                st->sum_top += stp * d->inv_nx;
+                st->samples += 1;
+                st->next_sample = t + (d->stress_every > 0 ? d->stress_every : 1);
             }
         }
+        __syncthreads();   // the samples have read the step counters
+    }
+    for (int l = tid; l < a.nlat; l += NT) {
+        DevStats* st = a.lat[l].st;
+        const long long t = l == tid ? t0 : st->t;
+        const int cur = l == tid ? cur0 : st->cur;
+        st->t = t + 1;
+        st->cur = cur ^ 1;
+        st->pull = 1;
     }
 }
 
@@ -1200,7 +1213,7 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
     if constexpr (!ALLPER) {
         __syncthreads();   // this CTA's wall-site values are written
         if (!s_fail) wall_sums<P, SPT>(a, a.cta_items[blockIdx.x], it_end, tid);
-    }
+    }   // (the barrier before the arrival orders the sums before it)
     if (STAGED && tid == kStoreThread) bulk_wait_all();
     if (s_fail && tid == 0) {
         // Let copies in flight land before the CTA exits.  No slot is
@@ -1214,16 +1227,22 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
     if (s_fail && tid == 0)   // report on every lattice of the launch
         for (int l = 0; l < a.nlat; ++l) atomicOr(&a.lat[l].st->err, ERR_TIMEOUT);
 
-    // The last CTA advances every lattice and takes the wall samples.
-    if (tid == 0) {
-        __threadfence();
-        s_last = atomicAdd(a.ticket, 1u) == (unsigned int)(G - 1);
+    // The last CTA advances every lattice and takes the wall samples.  Its
+    // step counters are loaded by every CTA now, off the launch's tail.
+    long long t0 = 0;
+    int cur0 = 0;
+    if (tid < a.nlat) {
+        const DevStats* st = a.lat[tid].st;
+        t0 = *((volatile const long long*)&st->t);
+        cur0 = *((volatile const int*)&st->cur);
     }
+    __syncthreads();   // this CTA's writes (wall sums, timeout flags) precede its arrival
+    if (tid == 0) s_last = ticket_arrive(a.ticket) == (unsigned int)(G - 1);
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
-    advance_lattices<P, ALLPER, L::NT>(a, tid);
-    __threadfence();
+    advance_lattices<P, ALLPER, L::NT>(a, tid, t0, cur0);
+    // no other CTA of the launch touches the ticket again; the next launch
+    // reads it after this one has completed
     if (tid == 0) *a.ticket = 0u;
 }
 

@@ -103,7 +103,7 @@ struct lb_pool {
     size_t budget;
     Arena arena;
     std::vector<Member> members;
-    // launch area: descriptors, arrival counter, per-item wall slots
+    // launch area: descriptors, arrival counter, item tables
     char* desc_mem;
     unsigned int* ticket;
     double* slots;
@@ -151,7 +151,7 @@ lb_status build(lb_pool* P, Choice c) {
     std::vector<Lattice*> lats;
     for (int j : P->active) lats.push_back(&P->members[(size_t)j].lat);
     const int nlat = (int)lats.size();
-    // slots: 2 per item; items are largest for seg = 1 (one per tile)
+    // item tables: items are most numerous for seg = 1 (one per tile)
     size_t tiles = 0, strips = 0;
     for (Lattice* L : lats) {
         tiles += (size_t)L->nstrips * (size_t)L->ntiles_y;
