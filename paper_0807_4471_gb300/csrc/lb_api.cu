@@ -1,6 +1,6 @@
 // lb_api.cu -- the single-lattice C ABI declared in include/lb.h: a handle is
 // one lattice region plus the step-launch area (arrival counter, lattice
-// descriptor, per-item wall slots) in one workspace.  The engine in
+// descriptor, item tables) in one workspace.  The engine in
 // lb_engine.cu does the work; every step of the model runs in the kernels.
 #include <cstring>
 #include <new>

@@ -821,8 +821,9 @@ __device__ __forceinline__ void block_sum4(double red[4], double (*s_red)[4]) {
 // carried forward as the next tile's first four; so each block is loaded
 // and each deviation row computed once per strip, and only the x halo (4 of
 // 64 columns) is redundant.  Every thread keeps one column and SPT rows of
-// the window in both phases, so all its shared-memory addresses within a
-// slot are fixed.  SPT = 2: each thread updates two vertically adjacent
+// the window (its own sites' cells, see t_m and t_w), so all its
+// shared-memory addresses within a slot are fixed.  SPT = 2: each thread
+// updates two vertically adjacent
 // sites, which share four of their six stencil rows.  Tiles leave through a
 // staging tile by TMA bulk tensor stores (one per 8 rows), clipped at the
 // lattice edge, and tiles near an edge then write the periodic ghost
