@@ -490,7 +490,9 @@ struct SiteOut {
 // carried as (A, B) pairs throughout.  TAU1 (omega = 1 for both species,
 // OBS = false): the collision needs the populations only through j, which the
 // caller passes in jg = {jx, jy} (in the storage scale); bm, b0 and bp are
-// not read.
+// not read.  Non-finite densities: the step (OBS = false) accumulates
+// 0 * rho into *nf, which turns NaN at an inf or NaN density and stays zero
+// otherwise; the observables set `bad`.
 template <int P, bool OBS, bool GEN, int PS, int SINK, bool TAU1 = false>
 __device__ __forceinline__ void site_update(
     const typename Prec<P>::T2* bm, const typename Prec<P>::T2* b0,
@@ -499,7 +501,7 @@ __device__ __forceinline__ void site_update(
     typename Prec<P>::C2 drho, int x, int y, bool per, int pull, const Geom& g,
     const LatVals<typename Prec<P>::C>& v, const Coef<typename Prec<P>::C>& k,
     const SiteOut<typename Prec<P>::T2>& o, double red[4], bool& bad,
-    const typename Prec<P>::C2* jg = nullptr) {
+    typename Prec<P>::C2* nf = nullptr, const typename Prec<P>::C2* jg = nullptr) {
     typedef typename Prec<P>::T2 T2;
     typedef typename Prec<P>::C C;
     typedef typename Prec<P>::C2 C2;
@@ -514,7 +516,11 @@ __device__ __forceinline__ void site_update(
         moments<P>(h, jx, jy);
     }
     const C2 rho = padd(pset(v.rho_ref), drho);
-    if (o.valid && !(isfinite(rho.x) && isfinite(rho.y))) bad = true;
+    if constexpr (OBS) {
+        if (o.valid && !(isfinite(rho.x) && isfinite(rho.y))) bad = true;
+    } else if (o.valid) {
+        *nf = pfma(rho, pset(C(0)), *nf);   // stays zero unless a density is inf or NaN
+    }
 
     // Eq. (2): F_s = -Psi_s(r) sum_d K_s(d) d Psi_s(r + d)
     //               - (G_X/rho0) rho_s(r) sum_d w(d) d rho_s'(r + d);
@@ -956,7 +962,7 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
         while (p_pos < released + L::NB && issue_next()) {}
     };
 
-    bool bad = false;
+    bool bad_unused = false;   // (the observables' flag; the step uses nf)
     int c_pos = 0;   // ring position of the current item's first block
     for (int it = a.cta_items[blockIdx.x]; it < it_end && !s_fail; ++it) {
         const int4 w = a.items[it];
@@ -972,6 +978,7 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
         // the step counter advances only after every CTA of the launch is done
         const uint32_t key = hash32((uint32_t)*((volatile long long*)&d->st->t) * 0x9e3779b9u);
         T2* fout = reinterpret_cast<T2*>(d->fbuf[cur ^ 1]);
+        C2 nf = pset(C(0));   // 0 * rho over the item's sites: NaN at a non-finite density
         // ring slot and phase parity of the tile's first block, kept as the
         // tiles advance
         int qm = c_pos % L::NB, qph = (c_pos / L::NB) & 1;
@@ -1108,13 +1115,12 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
                     const int lx = t_lx, ly = SPT * t_j;
                     const int x = x0 + lx, y = y0 + ly;
                     if (lx < L::TX && x < g.nx && y < g.ny) {
-                        const int bc = lx + L::GX;
                         C2 fx[SPT], fy[SPT], qx[SPT], qy[SPT], dp[SPT], dr[SPT];
                         force_sums<SPT, L::RX>(win_p + ly * L::RX + lx + 2,
                                                win_r + ly * L::RX + lx + 2, a.k, fx, fy, qx, qy, dp, dr);
                         SiteOut<T2> o;
                         o.rbits = 0u;
-                        uint32_t srh = 0u;   // the shared hash of this thread's sites
+                        [[maybe_unused]] uint32_t srh = 0u;   // the shared hash of this thread's sites
                         if constexpr (sizeof(T2) == 4) srh = sr_hash(key, x, y, g.nx);
                         o.obs = OBS_NONE;
                         o.valid = 1;
@@ -1147,12 +1153,13 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
                             if constexpr (TAU1) {
                                 site_update<P, false, GEN, PS, STAGED ? SINK_STAGE : SINK_GLOBAL, true>(
                                     nullptr, nullptr, nullptr, fx[s], fy[s], qx[s], qy[s], dp[s], dr[s],
-                                    x, ys, per, pull, g, v, a.k, o, wr, bad, jn[s]);
+                                    x, ys, per, pull, g, v, a.k, o, wr, bad_unused, &nf, jn[s]);
                             } else {
+                                const int bc = lx + L::GX;
                                 site_update<P, false, GEN, PS, STAGED ? SINK_STAGE : SINK_GLOBAL>(
                                     brow(ly + s + 2, bc), brow(ly + s + 3, bc), brow(ly + s + 4, bc),
                                     fx[s], fy[s], qx[s], qy[s], dp[s], dr[s], x, ys, per, pull, g, v,
-                                    a.k, o, wr, bad);
+                                    a.k, o, wr, bad_unused, &nf);
                             }
                         }
                         if constexpr (STAGED) fence_proxy_async();   // staging writes before the bulk store
@@ -1197,10 +1204,8 @@ __global__ void __launch_bounds__(Layout<P, SPT>::NT, 1)
                 qph ^= 1;
             }
         }
-        if (bad) {   // a density of this lattice went non-finite
+        if (!(nf.x == C(0) && nf.y == C(0)))   // a density of this lattice went non-finite
             atomicOr(&d->st->err, ERR_NONFINITE);
-            bad = false;
-        }
         if (s_fail) break;
         c_pos += SPT * (ty_b - ty_a) + 1;
     }

@@ -66,11 +66,6 @@ public:
             }
         }
     }
-    size_t largest() const {
-        size_t m = 0;
-        for (auto& kv : free_) m = std::max(m, kv.second);
-        return m;
-    }
 
 private:
     std::map<size_t, size_t> free_;
