@@ -488,7 +488,9 @@ def main():
 
     extra = {}
     if rank == 0 and not args.no_peak:
-        for p in ("fp32", "fp16"):
+        # FP32 and the two 16-bit offset formats (BF16: the same kernel code as
+        # FP16 with the other 16-bit type)
+        for p in ("fp32", "fp16", "bf16"):
             by_rows = {}
             for rows in (8, 16):
                 mlups, gbs = peak_lattice(torch, lb, p, lbinputs.CFG_PEAK["nx"], 50, rows)
