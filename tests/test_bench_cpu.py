@@ -65,3 +65,19 @@ def test_traffic_lookup_needs_matching_hash(monkeypatch):
 
 def test_replica_throughput_is_weak_scaling():
     assert bench.replica_throughput(100.0, 4, 2.0) == pytest.approx(200.0)
+
+
+def test_traffic_record_is_for_this_kernel_source():
+    """The DRAM traffic the bench reports comes from profiles/traffic.json,
+    taken with ncu on a given kernel source: every entry must carry the
+    current source's hash (else the bench reports traffic null and the
+    profiles describe another kernel)."""
+    import json
+    with open(os.path.join(bench.ROOT, "profiles", "traffic.json")) as fh:
+        rec = json.load(fh)
+    assert rec, "no traffic record"
+    h = bench.kernel_hash()
+    for key, e in rec.items():
+        assert e["kernel_sha"] == h, key
+        assert e["dram_bytes_per_launch"] > 0
+    assert bench.ncu_traffic("k_step", "fp32", "5x512x512") == rec["k_step:fp32:5x512x512"]["dram_bytes_per_launch"]
